@@ -1,0 +1,230 @@
+/*
+ * pat.h — C ABI of the GB300 (sm_103a) photoacoustic operator library.
+ *
+ * The library evaluates the discrete forward operator A of 2D photoacoustic
+ * tomography in a circular (possibly limited-view) detection geometry and its
+ * exact discrete adjoint A^T, plus the smoothed total-variation term used by
+ * the variational and deep-image-prior reconstructions.
+ *
+ *   Model.  Eq. (1) (Sec. 2.1) is the wave initial-value problem with initial
+ *   pressure f and zero initial velocity, observed on the detection curve by
+ *   Eq. (2); Eq. (3) writes the measurement as g = A f + delta.  With c = 1
+ *   the 2D Poisson formula gives
+ *       p(y, t) = d/dt  int_0^t  r (M f)(y, r) / sqrt(t^2 - r^2)  dr,
+ *   (M f)(y, r) the mean of f over the circle of radius r about detector y.
+ *   Limited view (Sec. 2.1): only detectors on an arc are present.
+ *
+ *   Discretisation (the paper defers it to its fast operators; this library
+ *   uses the following direct one):
+ *     - image N x N on [-1,1]^2, h = 2/N, pixel (iy, ix) centred at
+ *       (-1 + (ix+1/2) h, -1 + (iy+1/2) h), stored row-major f[iy*N + ix];
+ *     - detector j at angle theta0 + (j + 1/2) Phi / n_det on the unit circle
+ *       (cell-centred, matching the 256-on-270-degree array of Sec. 2.4.2);
+ *     - Delta = T / n_t, times t_k = k Delta (k = 1..n_t), radii r_m = m Delta
+ *       (m = 0..n_t+1);
+ *     - circular mean by the K-node periodic trapezoid rule over bilinear
+ *       samples of f (zero outside the grid);
+ *     - Abel integral by exact product integration of the piecewise-linear
+ *       mean, time derivative by the midpoint difference over +-Delta/2; the
+ *       weights are built once per plan in FP64 and stored in FP32.
+ *   Everything else runs in FP32 (optionally BF16 image storage, FP32 math).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA device addresses on the device that was current
+ *     when the plan was created, 16-byte aligned, owned by the caller.
+ *   - Host pointers are ordinary host addresses owned by the caller.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued asynchronously on it; no call synchronises the host
+ *     unless stated.
+ *   - Arguments are validated before anything is enqueued; an invalid call
+ *     returns an error status and enqueues nothing.  Errors reported by the
+ *     CUDA runtime while enqueueing map to PAT_ERR_CUDA.  Nothing throws.
+ *   - A plan holds one workspace: calls using the same plan must be ordered
+ *     (same stream or explicit events).  Different plans are independent.
+ *
+ * Layout of a plan with n_instances instances (see pat_plan_layout):
+ *   f (images):  instance i occupies N_i*N_i elements at f_offsets[i];
+ *   g (data):    instance i occupies n_det_i*n_t_i FP32 at g_offsets[i],
+ *                row j = detector, time fastest (g[j*n_t + (k-1)] = g(y_j, t_k)).
+ *   With identical geometries the offsets are i*N*N and i*n_det*n_t.
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pat_plan* pat_plan_t;
+
+typedef enum {
+    PAT_OK = 0,
+    PAT_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or geometry        */
+    PAT_ERR_CUDA = 2,        /* CUDA runtime error while enqueueing / creating  */
+    PAT_ERR_OOM = 3,         /* device or host allocation failed                */
+    PAT_ERR_UNSUPPORTED = 4, /* valid request this build does not implement     */
+    PAT_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
+    PAT_ERR_BAD_PLAN = 6     /* NULL, destroyed or foreign plan handle          */
+} pat_status_t;
+
+typedef enum { PAT_F32 = 0, PAT_BF16 = 1 } pat_dtype_t;
+
+/* Schedules for pat_forward / pat_adjoint. */
+typedef enum {
+    PAT_SCHED_STAGED = 0,     /* one launch per stage (circular means, time)   */
+    PAT_SCHED_PERSISTENT = 1  /* one persistent launch per operator (batched) */
+} pat_schedule_t;
+
+/* One acquisition geometry (one instance). */
+typedef struct {
+    int32_t n;         /* image side N (N x N pixels); multiple of 4 (8 for BF16), 8..4096 */
+    int32_t n_det;     /* detectors on the arc, 1..16384                                   */
+    double arc_start;  /* theta0 in radians                                                */
+    double arc_span;   /* Phi in radians, 0 < Phi <= 2 pi                                  */
+    int32_t n_t;       /* time samples on (0, t_max], 1..16384                             */
+    double t_max;      /* T > 0 (unit sound speed, unit detector radius)                   */
+    int32_t n_angles;  /* K angular quadrature nodes per circular mean, 3..65536           */
+} pat_geometry_t;
+
+/* Plan options; zero-initialised options select the defaults. */
+typedef struct {
+    int32_t image_dtype; /* pat_dtype_t: storage of f in pat_forward / pat_adjoint           */
+    int32_t schedule;    /* pat_schedule_t                                                   */
+    int32_t tune;        /* 0 = built-in tile shapes, 1 = time candidates at creation (needs  */
+                         /*     a stream; synchronises it), 2 = use tile fields below         */
+    int32_t m_lanes;     /* radii per warp in the circular-mean kernel (32, 16 or 8); 0=auto */
+    int32_t q_piece;     /* max angular nodes per work unit (multiple of 4); 0 = auto        */
+    int32_t band_rows;   /* max image rows per shared-memory band; 0 = auto                  */
+    int32_t adj_groups;  /* detector groups per adjoint CTA (1, 2 or 4); 0 = auto            */
+    int32_t reserved[9];
+} pat_options_t;
+
+/* Plan statistics (pat_plan_info). */
+typedef struct {
+    int32_t n_instances;
+    int32_t device;          /* CUDA ordinal the plan is bound to                         */
+    int64_t f_elems;         /* total image elements over all instances                   */
+    int64_t g_elems;         /* total data elements over all instances                    */
+    int64_t samples;         /* sum over instances of (j,m,q) samples touching the grid   */
+    int64_t sample_slots;    /* samples the circular-mean kernel evaluates (incl. waste)  */
+    int64_t time_macs;       /* multiply-adds of the two Abel stages per operator call    */
+    int64_t work_units;      /* circular-mean work units                                  */
+    int64_t device_bytes;    /* device memory held by the plan                            */
+    int32_t m_lanes, q_piece, band_rows, adj_groups; /* tile shape in use              */
+    int32_t bands_max;       /* largest number of bands of any instance                   */
+    int32_t reserved[7];
+} pat_plan_info_t;
+
+/*
+ * pat_plan_create — build the tables, weights and work lists for
+ * n_instances geometries (Eq. (1)-(3), Sec. 2.1) on the current device.
+ *   geoms:   host array of n_instances geometries (read only during the call).
+ *   opt:     host pointer or NULL for defaults.
+ *   stream:  used for the uploads (and autotuning); the call returns after
+ *            the uploads completed.
+ *   out:     receives the plan handle; unchanged on error.
+ * The Abel weights are computed once per distinct n_t in FP64 and rounded to
+ * FP32.  Errors: PAT_ERR_INVALID_ARG (geometry out of range, NULL out),
+ * PAT_ERR_OOM, PAT_ERR_CUDA.
+ */
+pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances,
+                             const pat_options_t* opt, void* stream, pat_plan_t* out);
+
+/* pat_plan_destroy — free a plan (after the work using it has completed).
+ * NULL returns PAT_ERR_BAD_PLAN; a destroyed handle must not be reused. */
+pat_status_t pat_plan_destroy(pat_plan_t plan);
+
+/*
+ * pat_plan_layout — element offsets of each instance in the packed f and g
+ * buffers.  f_offsets and g_offsets are host arrays of n_instances + 1
+ * entries (the last entry is the total); either may be NULL.
+ */
+pat_status_t pat_plan_layout(pat_plan_t plan, int64_t* f_offsets, int64_t* g_offsets);
+
+/* pat_plan_info — statistics and the tile shape chosen (host struct). */
+pat_status_t pat_plan_info(pat_plan_t plan, pat_plan_info_t* info);
+
+/*
+ * pat_forward — g = A f for every instance (Eq. (3) without noise).
+ *   d_f: device, packed images in the plan's image dtype (FP32 or BF16).
+ *   d_g: device, packed FP32 data, overwritten.
+ * Errors: PAT_ERR_BAD_PLAN, PAT_ERR_INVALID_ARG (NULL / misaligned), PAT_ERR_CUDA.
+ */
+pat_status_t pat_forward(pat_plan_t plan, const void* d_f, float* d_g, void* stream);
+
+/*
+ * pat_adjoint — f = A^T g for every instance: the exact transpose of the
+ * discrete A above, the operator whose application gives the data-term
+ * gradient of Eq. (4) and Eq. (5) (Sec. 2.2).  Evaluated as a gather over
+ * pixels (each output element is summed by one thread in a fixed order; no
+ * atomics), so results are deterministic.
+ *   d_g: device, packed FP32 data (read only).
+ *   d_f: device, packed images in the plan's image dtype, overwritten.
+ */
+pat_status_t pat_adjoint(pat_plan_t plan, const float* d_g, void* d_f, void* stream);
+
+/*
+ * pat_tv_grad — value and gradient of the smoothed isotropic total variation
+ *   TV(f) = sum_{i,j} sqrt(dx^2 + dy^2 + eps^2),
+ *   dx = f[i][j+1]-f[i][j], dy = f[i+1][j]-f[i][j] (zero on the last
+ *   column / row), the regulariser of Eq. (4) and Eq. (5).
+ *   d_f:     device FP32 images (packed like pat_forward's input).
+ *   eps:     smoothing, > 0.
+ *   d_grad:  device FP32, overwritten with dTV/df (may be NULL).
+ *   d_value: device FP32 array of n_instances values (may be NULL).
+ * FP32 plans only (PAT_ERR_UNSUPPORTED for BF16 plans).
+ */
+pat_status_t pat_tv_grad(pat_plan_t plan, const float* d_f, float eps, float* d_grad,
+                         float* d_value, void* stream);
+
+/*
+ * pat_residual — d_r = scale * (d_Af - d_g) over all packed data elements
+ * (the data-fit residual of Eq. (4); scale 2 gives the gradient factor of
+ * the un-halved data term of Eq. (5)).  In-place use (d_r == d_Af) is allowed.
+ */
+pat_status_t pat_residual(pat_plan_t plan, const float* d_Af, const float* d_g, float* d_r,
+                          float scale, void* stream);
+
+/*
+ * pat_descent_step — f <- f - tau * (d_adj + lam * d_tvgrad), then f <- max(f, 0)
+ * when nonneg != 0 (the constraint f >= 0 of Eq. (4)); FP32 images.
+ * d_tvgrad may be NULL (no TV term).  d_delta (nullable, device FP32, two
+ * values per instance) receives ||f_new - f_old||^2 and ||f_new||^2 for the
+ * relative-change stopping rule of Sec. 2.3.
+ */
+pat_status_t pat_descent_step(pat_plan_t plan, float* d_f, const float* d_adj,
+                              const float* d_tvgrad, float tau, float lam, int32_t nonneg,
+                              float* d_delta, void* stream);
+
+/*
+ * pat_plan_sync_status — synchronise the stream and report a device-side
+ * error recorded by a bounded wait in a persistent launch (PAT_ERR_TIMEOUT),
+ * clearing it.  Returns PAT_OK when none was recorded.
+ */
+pat_status_t pat_plan_sync_status(pat_plan_t plan, void* stream);
+
+/*
+ * Per-kernel timing (tracing).  When enabled, every kernel the plan enqueues
+ * is bracketed by a pair of CUDA events recorded on the launch stream.
+ * pat_plan_kernel_times synchronises those events, adds their elapsed times
+ * per kernel kind into total_ms[kind] and launch counts into launches[kind]
+ * (host arrays of n_kinds entries, either may be NULL) and forgets them.
+ * Kinds (pat_kernel_kind_t order): circular means, Abel forward, Abel
+ * adjoint, adjoint gather, TV, residual, descent step.
+ */
+typedef enum {
+    PAT_K_CIRCMEAN = 0, PAT_K_ABEL_FWD = 1, PAT_K_ABEL_ADJ = 2, PAT_K_ADJ_GATHER = 3,
+    PAT_K_TV = 4, PAT_K_RESIDUAL = 5, PAT_K_DESCENT = 6, PAT_K_COUNT = 7
+} pat_kernel_kind_t;
+pat_status_t pat_plan_set_timing(pat_plan_t plan, int32_t enable);
+pat_status_t pat_plan_kernel_times(pat_plan_t plan, double* total_ms, int64_t* launches, int32_t n_kinds);
+
+/* Human-readable name of a status code (static string). */
+const char* pat_status_string(pat_status_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAT_H */

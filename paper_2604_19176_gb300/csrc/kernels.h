@@ -1,0 +1,27 @@
+// kernels.h — launchers of the device kernels (host-callable, enqueue only).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pat_internal.h"
+
+namespace patgpu {
+
+constexpr int kCircThreads = 512;   // threads per circular-mean CTA (16 warps)
+
+cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st);
+cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st);
+cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st);
+cudaError_t launch_adjoint_gather(const DevPlan& dp, void* f, cudaStream_t st);
+cudaError_t launch_tv(const DevPlan& dp, const float* f, float eps, float* grad, float* value, cudaStream_t st);
+cudaError_t launch_residual(const float* a, const float* b, float* r, float scale, int64_t n, cudaStream_t st);
+cudaError_t launch_descent(const DevPlan& dp, float* f, const float* adj, const float* tvg, float tau, float lam,
+                           int nonneg, float* delta, cudaStream_t st);
+cudaError_t launch_count_samples(const DevPlan& dp, int inst_idx, int n_det, unsigned long long* out,
+                                 cudaStream_t st);
+
+// Occupancy of the circular-mean kernel for the plan's tile shape.
+int circmean_blocks_per_sm(int m_lanes, bool bf16, int smem_bytes);
+
+} // namespace patgpu

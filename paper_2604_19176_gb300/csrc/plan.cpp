@@ -1,0 +1,632 @@
+// plan.cpp — host-side plan builder: geometry tables, the FP64 Abel weights,
+// circular-mean work units, CTA schedules and tiles, device upload.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <queue>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "plan.h"
+
+namespace patgpu {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+template <typename F>
+void parallel_for(int n, F&& fn)
+{
+    int nt = (int)std::thread::hardware_concurrency();
+    nt = std::max(1, std::min(nt, 32));
+    if (n < 2 || nt == 1) {
+        for (int i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    for (int t = 0; t < std::min(nt, n); ++t)
+        th.emplace_back([&]() {
+            for (int i = next++; i < n; i = next++) fn(i);
+        });
+    for (auto& x : th) x.join();
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = kTwoPi / 2;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Product-integration weights w_m(tau) = int_0^tau hat_m(rho) rho / sqrt(tau^2 - rho^2) drho
+// (dimensionless; hat_m the piecewise-linear hat on the integer nodes).  The
+// substitution rho = tau sin(theta) turns each segment integral into the
+// smooth integral of hat(tau sin theta) tau sin theta over theta, evaluated
+// with Gauss-Legendre quadrature in FP64.
+void abel_weights_gl(double tau, int n_r, const std::vector<double>& gx, const std::vector<double>& gw,
+                     double* w)
+{
+    std::fill(w, w + n_r, 0.0);
+    for (int s = 0; s + 1 < n_r && (double)s < tau; ++s) {
+        const double a = s, b = std::min((double)(s + 1), tau);
+        const double ta = std::asin(a / tau), tb = std::asin(std::min(b / tau, 1.0));
+        const double half = 0.5 * (tb - ta), mid = 0.5 * (tb + ta);
+        double up = 0.0, dn = 0.0;
+        for (size_t i = 0; i < gx.size(); ++i) {
+            const double rho = tau * std::sin(mid + half * gx[i]);
+            const double wr = gw[i] * rho;
+            up += wr * (rho - a);
+            dn += wr * (a + 1.0 - rho);
+        }
+        w[s + 1] += half * up;
+        w[s] += half * dn;
+    }
+}
+
+// Abel-plus-midpoint-derivative matrix P (n_t x (n_t + 2)), FP64 -> FP32:
+// p(t_k) = (Q(t_k + Delta/2) - Q(t_k - Delta/2)) / Delta with Q the Abel
+// integral of the piecewise-linear circular mean; Delta cancels.
+std::vector<float> build_abel_matrix(int n_t)
+{
+    const int n_r = n_t + 2;
+    std::vector<double> gx, gw;
+    gauss_legendre(12, gx, gw);
+    std::vector<double> wt((size_t)(n_t + 1) * n_r);
+    parallel_for(n_t + 1, [&](int i) { abel_weights_gl(i + 0.5, n_r, gx, gw, &wt[(size_t)i * n_r]); });
+    std::vector<float> P((size_t)n_t * n_r);
+    for (int k = 1; k <= n_t; ++k)
+        for (int m = 0; m < n_r; ++m)
+            P[(size_t)(k - 1) * n_r + m] = (float)(wt[(size_t)k * n_r + m] - wt[(size_t)(k - 1) * n_r + m]);
+    return P;
+}
+
+struct GeomKey {
+    int n, n_det, n_t, K, bf16, ml, qp, rows;
+    double a0, span, tmax;
+    bool operator<(const GeomKey& o) const
+    {
+        return std::tie(n, n_det, n_t, K, bf16, ml, qp, rows, a0, span, tmax) <
+               std::tie(o.n, o.n_det, o.n_t, o.K, o.bf16, o.ml, o.qp, o.rows, o.a0, o.span, o.tmax);
+    }
+};
+
+struct BandTemplate {
+    int lo, hi;                      // cell rows [lo, hi)
+    std::vector<Unit> units;         // reordered into segments
+    std::vector<std::pair<int, int>> seg_ranges; // [begin, end) within units
+    std::vector<double> seg_cost;
+    double cost = 0.0;
+};
+
+struct GeomTemplate {
+    std::vector<BandTemplate> bands;
+    std::vector<int32_t> slotcnt;    // n_det x nmb
+    int n_slots = 0;
+    int nmb = 0;
+    int64_t unit_base = 0;           // offset of band 0's units in the global unit array
+    std::vector<int64_t> band_unit_base;
+    int64_t slot_samples = 0;        // lane-samples the circular-mean kernel evaluates
+};
+
+constexpr double kUnitOverhead = 24.0; // per-unit fixed cost, in angle iterations
+
+// Angular chunks (of `G` consecutive q) whose annular sector (radii
+// [rlo, rhi] about (U, V)) can reach the rectangle [x0, x1] x [y0, y1]:
+// conservative test on the sector's bounding box.
+void mark_chunks(double U, double V, double rlo, double rhi, double x0, double x1, double y0, double y1, int K,
+                 int G, std::vector<uint8_t>& mark)
+{
+    const int nch = (K + G - 1) / G;
+    mark.assign(nch, 0);
+    // quick reject: the annulus misses the rectangle entirely
+    const double cx = std::min(std::max(U, x0), x1), cy = std::min(std::max(V, y0), y1);
+    const double dmin = std::hypot(cx - U, cy - V);
+    const double fx = std::max(std::fabs(x0 - U), std::fabs(x1 - U));
+    const double fy = std::max(std::fabs(y0 - V), std::fabs(y1 - V));
+    const double dmax = std::hypot(fx, fy);
+    if (rhi < dmin || rlo > dmax) return;
+    const double pi = kTwoPi / 2;
+    for (int c = 0; c < nch; ++c) {
+        const int qa = c * G, qb = std::min((c + 1) * G, K) - 1;
+        const double pa = kTwoPi * qa / K, pb = kTwoPi * qb / K;
+        double cmin = std::min(std::cos(pa), std::cos(pb)), cmax = std::max(std::cos(pa), std::cos(pb));
+        double smin = std::min(std::sin(pa), std::sin(pb)), smax = std::max(std::sin(pa), std::sin(pb));
+        if (pa <= pi && pi <= pb) cmin = -1.0;
+        if (pa <= 0.5 * pi && 0.5 * pi <= pb) smax = 1.0;
+        if (pa <= 1.5 * pi && 1.5 * pi <= pb) smin = -1.0;
+        if (pa == 0.0) cmax = 1.0;
+        const double bx0 = U + std::min(rlo * cmin, rhi * cmin), bx1 = U + std::max(rlo * cmax, rhi * cmax);
+        const double by0 = V + std::min(rlo * smin, rhi * smin), by1 = V + std::max(rlo * smax, rhi * smax);
+        if (bx1 >= x0 && bx0 <= x1 && by1 >= y0 && by0 <= y1) mark[c] = 1;
+    }
+}
+
+} // namespace
+
+static_assert(sizeof(InstDev) % 8 == 0, "InstDev layout");
+
+pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const pat_options_t& opt,
+                        cudaStream_t st)
+{
+    P.n_inst = n_inst;
+    P.geoms.assign(geoms, geoms + n_inst);
+    P.opt = opt;
+    const bool bf16 = opt.image_dtype == PAT_BF16;
+    const int ml = opt.m_lanes;
+    const int qpiece = opt.q_piece;
+    const int esize = bf16 ? 2 : 4;
+    const int G = 4;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PAT_ERR_CUDA;
+    P.device = dev;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return PAT_ERR_CUDA;
+    P.num_sms = prop.multiProcessorCount;
+    P.max_smem_optin = (int)prop.sharedMemPerBlockOptin;
+
+    // ---- offsets ----------------------------------------------------------
+    P.f_offsets.assign(n_inst + 1, 0);
+    P.g_offsets.assign(n_inst + 1, 0);
+    for (int i = 0; i < n_inst; ++i) {
+        P.f_offsets[i + 1] = P.f_offsets[i] + (int64_t)geoms[i].n * geoms[i].n;
+        P.g_offsets[i + 1] = P.g_offsets[i] + (int64_t)geoms[i].n_det * geoms[i].n_t;
+    }
+
+    // ---- distinct K (trig) and n_t (Abel matrices) ------------------------
+    std::map<int, int64_t> trig_off, p_off;
+    std::vector<float2> trig;
+    std::vector<float> pmat;
+    for (int i = 0; i < n_inst; ++i) {
+        const int K = geoms[i].n_angles;
+        if (!trig_off.count(K)) {
+            trig_off[K] = (int64_t)trig.size();
+            for (int q = 0; q < 2 * K; ++q) {
+                const int qq = q % K;
+                const double ph = kTwoPi * qq / K;
+                trig.push_back(make_float2((float)std::cos(ph), (float)std::sin(ph)));
+            }
+        }
+        const int nt = geoms[i].n_t;
+        if (!p_off.count(nt)) {
+            p_off[nt] = (int64_t)pmat.size();
+            std::vector<float> Pm = build_abel_matrix(nt);
+            pmat.insert(pmat.end(), Pm.begin(), Pm.end());
+        }
+    }
+
+    // ---- per-geometry templates (units, bands, slots) ---------------------
+    // Band rows: the shared band of a CTA holds at most `rows` image rows.
+    std::map<GeomKey, int> tmpl_index;
+    std::vector<GeomTemplate> tmpls;
+    std::vector<int> inst_tmpl(n_inst);
+    std::vector<float> detU, detV;
+    std::vector<InstDev> inst(n_inst);
+    int smem_bytes = 0;
+    int bands_max = 0;
+
+    for (int i = 0; i < n_inst; ++i) {
+        const pat_geometry_t& g = geoms[i];
+        const int n = g.n;
+        const int W = bf16 ? band_pitch_bf16(n) : band_pitch_f32(n);
+        int rows_max = opt.band_rows > 0 ? opt.band_rows : (P.band_budget_bytes / (W * esize));
+        rows_max = std::max(rows_max, 3);
+        rows_max = std::min(rows_max, n + 2);
+        const int nb = (n + 1 + (rows_max - 1) - 1) / (rows_max - 1);
+        bands_max = std::max(bands_max, nb);
+
+        InstDev& d = inst[i];
+        std::memset(&d, 0, sizeof(d));
+        d.n = n;
+        d.n_det = g.n_det;
+        d.n_t = g.n_t;
+        d.n_r = g.n_t + 2;
+        d.K = g.n_angles;
+        d.c0 = n / 2;
+        const double delta = g.t_max * n / (2.0 * g.n_t); // r_m / h = m * delta
+        d.delta = (float)delta;
+        d.inv_delta = (float)(1.0 / (double)d.delta);
+        d.dphi = (float)(kTwoPi / g.n_angles);
+        d.inv_dphi = (float)(g.n_angles / kTwoPi);
+        d.inv_K = (float)(1.0 / g.n_angles);
+        d.nmb = (d.n_r + ml - 1) / ml;
+        d.f_off = P.f_offsets[i];
+        d.g_off = P.g_offsets[i];
+        d.p_off = p_off[g.n_t];
+        d.trig_off = (int32_t)trig_off[g.n_angles];
+        d.det_off = (int32_t)detU.size();
+        for (int j = 0; j < g.n_det; ++j) {
+            const double th = g.arc_start + (j + 0.5) * g.arc_span / g.n_det;
+            detU.push_back((float)(std::cos(th) * (n / 2.0) - 0.5));
+            detV.push_back((float)(std::sin(th) * (n / 2.0) - 0.5));
+        }
+
+        GeomKey key{n, g.n_det, g.n_t, g.n_angles, bf16 ? 1 : 0, ml, qpiece, rows_max, g.arc_start, g.arc_span,
+                    g.t_max};
+        auto it = tmpl_index.find(key);
+        if (it != tmpl_index.end()) {
+            inst_tmpl[i] = it->second;
+            continue;
+        }
+        const int ti = (int)tmpls.size();
+        tmpl_index[key] = ti;
+        inst_tmpl[i] = ti;
+        tmpls.emplace_back();
+        GeomTemplate& T = tmpls.back();
+        T.nmb = d.nmb;
+        T.bands.resize(nb);
+        for (int b = 0; b < nb; ++b) {
+            T.bands[b].lo = -1 + (int)(((int64_t)b * (n + 1)) / nb);
+            T.bands[b].hi = -1 + (int)(((int64_t)(b + 1) * (n + 1)) / nb);
+            const int rows = T.bands[b].hi - T.bands[b].lo + 1;
+            smem_bytes = std::max(smem_bytes, rows * W * esize);
+        }
+        // Units: for every (band, detector, radius block) the angle chunks
+        // whose sector can reach the band's cells, split into pieces.
+        const int c0 = n / 2;
+        const double eps = 0.01;
+        const int K = g.n_angles;
+        std::vector<std::vector<std::vector<Unit>>> per(nb, std::vector<std::vector<Unit>>(g.n_det));
+        const float* Uj = &detU[d.det_off];
+        const float* Vj = &detV[d.det_off];
+        parallel_for(g.n_det, [&](int j) {
+            std::vector<uint8_t> mark;
+            for (int b = 0; b < nb; ++b) {
+                const double x0 = -1.0 - c0 - eps, x1 = (double)(n - c0) + eps;
+                const double y0 = (double)(T.bands[b].lo - c0) - eps, y1 = (double)(T.bands[b].hi - c0) + eps;
+                for (int mb = 0; mb < d.nmb; ++mb) {
+                    const int m0 = mb * ml, m1 = std::min(m0 + ml, d.n_r) - 1;
+                    mark_chunks(Uj[j], Vj[j], m0 * (double)d.delta - eps, m1 * (double)d.delta + eps, x0, x1, y0, y1,
+                                K, G, mark);
+                    const int nch = (int)mark.size();
+                    // runs of marked chunks, with wrap-around
+                    std::vector<std::pair<int, int>> runs; // [c_begin, c_end) possibly c_end > nch for wrap
+                    int c = 0;
+                    while (c < nch) {
+                        if (!mark[c]) { ++c; continue; }
+                        int e = c;
+                        while (e < nch && mark[e]) ++e;
+                        runs.emplace_back(c, e);
+                        c = e;
+                    }
+                    if (runs.size() >= 2 && runs.front().first == 0 && runs.back().second == nch) {
+                        runs.back().second = nch + runs.front().second;
+                        runs.erase(runs.begin());
+                    }
+                    for (auto& r : runs) {
+                        int q0 = r.first * G;
+                        const int q1 = (r.second > nch) ? K + std::min((r.second - nch) * G, K)
+                                                        : std::min(r.second * G, K);
+                        int len = std::min(q1 - q0, K);
+                        while (len > 0) {
+                            const int piece = std::min(len, qpiece);
+                            Unit u{};
+                            u.j = j;
+                            u.m0 = m0;
+                            u.q0 = q0 % K;
+                            u.nq = piece;
+                            per[b][j].push_back(u);
+                            q0 += piece;
+                            len -= piece;
+                        }
+                    }
+                }
+            }
+        });
+        // slots per (detector, radius block), counted across bands in order
+        T.slotcnt.assign((size_t)g.n_det * d.nmb, 0);
+        for (int b = 0; b < nb; ++b)
+            for (int j = 0; j < g.n_det; ++j)
+                for (Unit& u : per[b][j]) {
+                    int32_t& c = T.slotcnt[(size_t)j * d.nmb + u.m0 / ml];
+                    u.slot = c++;
+                    T.n_slots = std::max(T.n_slots, (int)c);
+                    T.slot_samples += (int64_t)u.nq * ml;
+                }
+        for (int b = 0; b < nb; ++b) {
+            auto& band = T.bands[b];
+            for (int j = 0; j < g.n_det; ++j)
+                band.units.insert(band.units.end(), per[b][j].begin(), per[b][j].end());
+            for (const Unit& u : band.units) band.cost += u.nq + kUnitOverhead;
+        }
+    }
+
+    // ---- CTA schedule for the circular means ------------------------------
+    if (smem_bytes > P.max_smem_optin) return PAT_ERR_UNSUPPORTED;
+    P.fwd_smem = smem_bytes;
+    int bps = circmean_blocks_per_sm(ml, bf16, smem_bytes);
+    if (bps < 1) return PAT_ERR_UNSUPPORTED;
+    const int n_ctas_target = bps * P.num_sms;
+    double total_cost = 0.0;
+    for (int i = 0; i < n_inst; ++i)
+        for (auto& b : tmpls[inst_tmpl[i]].bands) total_cost += b.cost;
+    const double seg_target = std::max(1.0, total_cost / (2.0 * n_ctas_target));
+    // split each template band into segments (units dealt round-robin by cost)
+    for (auto& T : tmpls)
+        for (auto& band : T.bands) {
+            std::vector<Unit>& us = band.units;
+            std::stable_sort(us.begin(), us.end(), [](const Unit& a, const Unit& b) { return a.nq > b.nq; });
+            const int nseg = std::max(1, std::min((int)us.size(), (int)std::lround(band.cost / seg_target)));
+            std::vector<std::vector<Unit>> bins(nseg);
+            std::vector<double> cost(nseg, 0.0);
+            for (const Unit& u : us) {
+                const int k = (int)(std::min_element(cost.begin(), cost.end()) - cost.begin());
+                bins[k].push_back(u);
+                cost[k] += u.nq + kUnitOverhead;
+            }
+            us.clear();
+            for (int k = 0; k < nseg; ++k) {
+                if (bins[k].empty()) continue;
+                band.seg_ranges.emplace_back((int)us.size(), (int)(us.size() + bins[k].size()));
+                band.seg_cost.push_back(cost[k]);
+                us.insert(us.end(), bins[k].begin(), bins[k].end());
+            }
+        }
+    // global unit array
+    std::vector<Unit> units;
+    for (auto& T : tmpls) {
+        T.band_unit_base.resize(T.bands.size());
+        for (size_t b = 0; b < T.bands.size(); ++b) {
+            T.band_unit_base[b] = (int64_t)units.size();
+            units.insert(units.end(), T.bands[b].units.begin(), T.bands[b].units.end());
+        }
+    }
+    // segments of every instance, LPT-assigned to CTAs
+    struct SegC {
+        Segment s;
+        double cost;
+    };
+    std::vector<SegC> segc;
+    for (int i = 0; i < n_inst; ++i) {
+        const GeomTemplate& T = tmpls[inst_tmpl[i]];
+        for (size_t b = 0; b < T.bands.size(); ++b)
+            for (size_t k = 0; k < T.bands[b].seg_ranges.size(); ++k) {
+                Segment s{};
+                s.inst = i;
+                s.band_lo = T.bands[b].lo;
+                s.band_hi = T.bands[b].hi;
+                s.unit_begin = (int32_t)(T.band_unit_base[b] + T.bands[b].seg_ranges[k].first);
+                s.unit_end = (int32_t)(T.band_unit_base[b] + T.bands[b].seg_ranges[k].second);
+                segc.push_back({s, T.bands[b].seg_cost[k]});
+            }
+    }
+    std::stable_sort(segc.begin(), segc.end(), [](const SegC& a, const SegC& b) { return a.cost > b.cost; });
+    const int n_ctas = std::max(1, std::min(n_ctas_target, (int)segc.size()));
+    std::vector<std::vector<Segment>> cta_lists(n_ctas);
+    {
+        using E = std::pair<double, int>;
+        std::priority_queue<E, std::vector<E>, std::greater<E>> pq;
+        for (int c = 0; c < n_ctas; ++c) pq.push({0.0, c});
+        for (const SegC& s : segc) {
+            E e = pq.top();
+            pq.pop();
+            cta_lists[e.second].push_back(s.s);
+            pq.push({e.first + s.cost + 4.0 * kUnitOverhead, e.second});
+        }
+    }
+    std::vector<Segment> segs;
+    std::vector<int32_t> cta_seg(1, 0);
+    for (auto& l : cta_lists) {
+        segs.insert(segs.end(), l.begin(), l.end());
+        cta_seg.push_back((int32_t)segs.size());
+    }
+    if (segc.empty()) cta_seg.assign(1, 0);
+
+    // ---- per-instance workspace offsets and slot counts -------------------
+    std::vector<int32_t> slotcnt;
+    std::map<int, int64_t> tmpl_slot_off;
+    int64_t mpart_total = 0, mbar_total = 0;
+    int64_t samples_slots = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const int ti = inst_tmpl[i];
+        GeomTemplate& T = tmpls[ti];
+        if (!tmpl_slot_off.count(ti)) {
+            tmpl_slot_off[ti] = (int64_t)slotcnt.size() * 4;
+            slotcnt.insert(slotcnt.end(), T.slotcnt.begin(), T.slotcnt.end());
+        }
+        InstDev& d = inst[i];
+        d.slotcnt_off = tmpl_slot_off[ti];
+        d.n_slots = T.n_slots;
+        d.mpart_off = mpart_total;
+        mpart_total += (int64_t)T.n_slots * d.n_det * d.n_r;
+        d.mbar_off = mbar_total;
+        mbar_total += (int64_t)d.n_det * d.n_r;
+        samples_slots += T.slot_samples;
+    }
+
+    // ---- tiles ------------------------------------------------------------
+    std::vector<TimeTile> fwd_tiles, adj_tiles;
+    std::vector<AdjTile> gtiles;
+    std::vector<ImgTile> itiles;
+    int64_t time_macs = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const InstDev& d = inst[i];
+        for (int j0 = 0; j0 < d.n_det; j0 += 16) {
+            for (int k0 = 0; k0 < d.n_t; k0 += 64) fwd_tiles.push_back({i, j0, k0, 0});
+            for (int m0 = 0; m0 < d.n_r; m0 += 64) adj_tiles.push_back({i, j0, m0, 0});
+        }
+        for (int y0 = 0; y0 < d.n; y0 += kAdjOut)
+            for (int x0 = 0; x0 < d.n; x0 += kAdjOut) gtiles.push_back({i, x0, y0, 0});
+        for (int y0 = 0; y0 < d.n; y0 += 8)
+            for (int x0 = 0; x0 < d.n; x0 += 32) itiles.push_back({i, x0, y0, 0});
+        // nonzeros of P: rows kk have m <= kk + 2 (kk = k - 1)
+        int64_t nnz = 0;
+        for (int kk = 0; kk < d.n_t; ++kk) nnz += std::min(kk + 3, d.n_r);
+        time_macs += nnz * d.n_det;
+    }
+    // largest instances first for better tail behaviour
+    std::stable_sort(gtiles.begin(), gtiles.end(),
+                     [&](const AdjTile& a, const AdjTile& b) { return inst[a.inst].n_det > inst[b.inst].n_det; });
+
+    // ---- upload -----------------------------------------------------------
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = 0;
+    auto reserve = [&](size_t bytes) {
+        const size_t o = off;
+        off = align(off + std::max<size_t>(bytes, 1));
+        return o;
+    };
+    const size_t o_inst = reserve(sizeof(InstDev) * inst.size());
+    const size_t o_detU = reserve(sizeof(float) * detU.size());
+    const size_t o_detV = reserve(sizeof(float) * detV.size());
+    const size_t o_trig = reserve(sizeof(float2) * trig.size());
+    const size_t o_P = reserve(sizeof(float) * pmat.size());
+    const size_t o_slot = reserve(sizeof(int32_t) * slotcnt.size());
+    const size_t o_units = reserve(sizeof(Unit) * units.size());
+    const size_t o_segs = reserve(sizeof(Segment) * segs.size());
+    const size_t o_ctaseg = reserve(sizeof(int32_t) * cta_seg.size());
+    const size_t o_ft = reserve(sizeof(TimeTile) * fwd_tiles.size());
+    const size_t o_at = reserve(sizeof(TimeTile) * adj_tiles.size());
+    const size_t o_gt = reserve(sizeof(AdjTile) * gtiles.size());
+    const size_t o_it = reserve(sizeof(ImgTile) * itiles.size());
+    const size_t o_status = reserve(64);
+    const size_t o_count = reserve(64);
+    P.tables_bytes = off;
+    if (cudaMalloc(&P.d_tables, P.tables_bytes) != cudaSuccess) {
+        P.d_tables = nullptr;
+        cudaGetLastError();
+        return PAT_ERR_OOM;
+    }
+    std::vector<unsigned char> host(P.tables_bytes, 0);
+    auto put = [&](size_t o, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(host.data() + o, src, bytes);
+    };
+    put(o_inst, inst.data(), sizeof(InstDev) * inst.size());
+    put(o_detU, detU.data(), sizeof(float) * detU.size());
+    put(o_detV, detV.data(), sizeof(float) * detV.size());
+    put(o_trig, trig.data(), sizeof(float2) * trig.size());
+    put(o_P, pmat.data(), sizeof(float) * pmat.size());
+    put(o_slot, slotcnt.data(), sizeof(int32_t) * slotcnt.size());
+    put(o_units, units.data(), sizeof(Unit) * units.size());
+    put(o_segs, segs.data(), sizeof(Segment) * segs.size());
+    put(o_ctaseg, cta_seg.data(), sizeof(int32_t) * cta_seg.size());
+    put(o_ft, fwd_tiles.data(), sizeof(TimeTile) * fwd_tiles.size());
+    put(o_at, adj_tiles.data(), sizeof(TimeTile) * adj_tiles.size());
+    put(o_gt, gtiles.data(), sizeof(AdjTile) * gtiles.size());
+    put(o_it, itiles.data(), sizeof(ImgTile) * itiles.size());
+    if (cudaMemcpyAsync(P.d_tables, host.data(), P.tables_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return PAT_ERR_CUDA;
+
+    const int64_t tv_parts = 2 * (int64_t)itiles.size();
+    P.work_floats = mpart_total + mbar_total + tv_parts;
+    if (cudaMalloc(&P.d_work, sizeof(float) * std::max<int64_t>(P.work_floats, 1)) != cudaSuccess) {
+        P.d_work = nullptr;
+        cudaGetLastError();
+        return PAT_ERR_OOM;
+    }
+
+    unsigned char* base = static_cast<unsigned char*>(P.d_tables);
+    DevPlan& dp = P.dp;
+    std::memset(&dp, 0, sizeof(dp));
+    dp.inst = reinterpret_cast<const InstDev*>(base + o_inst);
+    dp.detU = reinterpret_cast<const float*>(base + o_detU);
+    dp.detV = reinterpret_cast<const float*>(base + o_detV);
+    dp.trig = reinterpret_cast<const float2*>(base + o_trig);
+    dp.P = reinterpret_cast<const float*>(base + o_P);
+    dp.slotcnt = reinterpret_cast<const uint8_t*>(base + o_slot);
+    dp.units = reinterpret_cast<const Unit*>(base + o_units);
+    dp.segs = reinterpret_cast<const Segment*>(base + o_segs);
+    dp.cta_seg = reinterpret_cast<const int32_t*>(base + o_ctaseg);
+    dp.fwd_tiles = reinterpret_cast<const TimeTile*>(base + o_ft);
+    dp.adj_tiles = reinterpret_cast<const TimeTile*>(base + o_at);
+    dp.gather_tiles = reinterpret_cast<const AdjTile*>(base + o_gt);
+    dp.img_tiles = reinterpret_cast<const ImgTile*>(base + o_it);
+    dp.mpart = P.d_work;
+    dp.mbar = P.d_work + mpart_total;
+    dp.tv_partial = P.d_work + mpart_total + mbar_total;
+    dp.status = reinterpret_cast<int32_t*>(base + o_status);
+    dp.n_inst = n_inst;
+    dp.n_fwd_ctas = (int)cta_seg.size() - 1;
+    dp.n_fwd_tiles = (int)fwd_tiles.size();
+    dp.n_adj_tiles = (int)adj_tiles.size();
+    dp.n_gather_tiles = (int)gtiles.size();
+    dp.n_img_tiles = (int)itiles.size();
+    dp.m_lanes = ml;
+    dp.adj_groups = opt.adj_groups;
+    dp.fwd_smem_bytes = smem_bytes;
+    dp.bf16 = bf16 ? 1 : 0;
+
+    // ---- sample count (exact, with the kernels' FP32 arithmetic) ----------
+    unsigned long long* d_count = reinterpret_cast<unsigned long long*>(base + o_count);
+    if (cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PAT_ERR_CUDA;
+    for (int i = 0; i < n_inst; ++i)
+        if (launch_count_samples(dp, i, inst[i].n_det, d_count, st) != cudaSuccess) return PAT_ERR_CUDA;
+    unsigned long long count = 0;
+    if (cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return PAT_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
+
+    // ---- info -------------------------------------------------------------
+    pat_plan_info_t& I = P.info;
+    std::memset(&I, 0, sizeof(I));
+    I.n_instances = n_inst;
+    I.device = dev;
+    I.f_elems = P.f_offsets[n_inst];
+    I.g_elems = P.g_offsets[n_inst];
+    I.samples = (int64_t)count;
+    I.sample_slots = samples_slots;
+    I.time_macs = time_macs;
+    I.work_units = (int64_t)units.size();
+    I.device_bytes = (int64_t)P.tables_bytes + (int64_t)sizeof(float) * P.work_floats;
+    I.m_lanes = ml;
+    I.q_piece = qpiece;
+    I.band_rows = 0;
+    for (auto& T : tmpls)
+        for (auto& b : T.bands) I.band_rows = std::max(I.band_rows, b.hi - b.lo + 1);
+    I.adj_groups = opt.adj_groups;
+    I.bands_max = bands_max;
+    return PAT_OK;
+}
+
+void free_plan_memory(Plan& P)
+{
+    for (auto& v : P.recorded)
+        for (auto& e : v) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+    for (auto e : P.event_pool) cudaEventDestroy(e);
+    for (auto& v : P.recorded) v.clear();
+    P.event_pool.clear();
+    if (P.d_tables) cudaFree(P.d_tables);
+    if (P.d_work) cudaFree(P.d_work);
+    P.d_tables = nullptr;
+    P.d_work = nullptr;
+}
+
+} // namespace patgpu

@@ -1,0 +1,67 @@
+"""CPU-only checks of the C ABI: the library builds and loads, exports every
+symbol include/pat.h declares, and validates arguments on the host before
+touching the GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "pat.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:pat_status_t|const char\*)\s+(pat_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2604_19176_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_expected_calls():
+    syms = declared_symbols()
+    from paper_2604_19176_gb300._lib import EXPORTED
+
+    assert set(syms) == set(EXPORTED)
+    for core in ("pat_plan_create", "pat_forward", "pat_adjoint", "pat_tv_grad", "pat_plan_destroy"):
+        assert core in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    assert lib.pat_status_string(0) == b"PAT_OK"
+    assert lib.pat_status_string(6) == b"PAT_ERR_BAD_PLAN"
+    assert lib.pat_status_string(99) == b"PAT_ERR_UNKNOWN"
+
+
+def test_host_validation_without_gpu(lib):
+    from paper_2604_19176_gb300 import _lib
+
+    h = ctypes.c_void_p()
+    geom = _lib.PatGeometry(64, 8, 0.0, 3.14, 16, 2.0, 16)
+    assert lib.pat_plan_create(None, 1, None, None, ctypes.byref(h)) == 1
+    assert lib.pat_plan_create(ctypes.byref(geom), 0, None, None, ctypes.byref(h)) == 1
+    assert lib.pat_plan_create(ctypes.byref(geom), 1, None, None, None) == 1
+    bad = _lib.PatGeometry(64, 8, 0.0, 3.14, 16, -1.0, 16)
+    assert lib.pat_plan_create(ctypes.byref(bad), 1, None, None, ctypes.byref(h)) == 1
+    opt = _lib.PatOptions()
+    opt.m_lanes = 5
+    assert lib.pat_plan_create(ctypes.byref(geom), 1, ctypes.byref(opt), None, ctypes.byref(h)) == 1
+    # calls on a handle that is not a live plan
+    assert lib.pat_forward(None, None, None, None) == 6
+    assert lib.pat_adjoint(ctypes.c_void_p(12345), None, None, None) == 6
+    assert lib.pat_tv_grad(None, None, ctypes.c_float(1e-3), None, None, None) == 6
+    assert lib.pat_plan_destroy(None) == 6
+    assert lib.pat_plan_info(None, None) == 6

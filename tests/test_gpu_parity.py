@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA operators (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 unless stated):
+  FP32 forward / adjoint            <= 1e-5
+  GPU adjoint identity              <= 1e-5
+  BF16 image storage vs the oracle on the BF16-rounded image  <= 1e-5
+  BF16 image storage vs the oracle on the FP32 image          <= 4e-3
+Inputs are FP32-rounded before the oracle sees them, so the tolerance
+measures the kernels' arithmetic, not the input rounding.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2604_19176_gb300 import Geometry, PatPlan, inputs
+from paper_2604_19176_gb300.workloads import gauss64_full, vessel256_half
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def og(g: Geometry) -> O.Geometry:
+    return O.Geometry(g.n, g.n_det, g.arc_start, g.arc_span, g.n_t, g.t_max, g.n_angles)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_fwd(plan, f, dev):
+    out = plan.forward(torch.tensor(f, dtype=plan.image_dtype, device=dev))
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy()
+
+
+def run_adj(plan, g, dev):
+    out = plan.adjoint(torch.tensor(g, dtype=torch.float32, device=dev))
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy()
+
+
+def test_forward_adjoint_gauss64(cuda_dev):
+    wl = gauss64_full()
+    g = wl.geometries[0]
+    f = f32(wl.phantoms()[0])
+    d = f32(inputs.random_data(g.n_det, g.n_t, seed=21))
+    plan = PatPlan(g, device=cuda_dev)
+    assert rel(run_fwd(plan, f, cuda_dev), O.forward(og(g), f)) <= TOL
+    assert rel(run_adj(plan, d, cuda_dev), O.adjoint(og(g), d)) <= TOL
+
+
+def test_forward_adjoint_vessel256_full_size(cuda_dev):
+    """The benchmark geometry at full size, elementwise against the oracle."""
+    O.set_threads(8)
+    wl = vessel256_half()
+    g = wl.geometries[0]
+    f = f32(wl.phantoms()[0])
+    d = f32(inputs.random_data(g.n_det, g.n_t, seed=22))
+    plan = PatPlan(g, device=cuda_dev)
+    gf = run_fwd(plan, f, cuda_dev)
+    ref = O.forward(og(g), f)
+    assert rel(gf, ref) <= TOL
+    assert np.max(np.abs(gf - ref)) <= 2e-5 * np.max(np.abs(ref))
+    fa = run_adj(plan, d, cuda_dev)
+    refa = O.adjoint(og(g), d)
+    assert rel(fa, refa) <= TOL
+    assert np.max(np.abs(fa - refa)) <= 2e-5 * np.max(np.abs(refa))
+    O.set_threads(1)
+
+
+@pytest.mark.parametrize("kw", [dict(m_lanes=16), dict(m_lanes=8), dict(q_piece=4), dict(band_rows=5),
+                                dict(band_rows=17, m_lanes=8, q_piece=12), dict(adj_groups=1), dict(adj_groups=2)])
+def test_tile_shapes_agree_with_oracle(cuda_dev, kw):
+    g = Geometry(48, 24, 0.4, 1.3 * math.pi, 80, 2.0, 70)
+    f = f32(inputs.gaussian_phantom(48, 5, seed=3) + 0.1 * inputs.random_image(48, seed=4))
+    d = f32(inputs.random_data(g.n_det, g.n_t, seed=5))
+    plan = PatPlan(g, device=cuda_dev, **kw)
+    assert rel(run_fwd(plan, f, cuda_dev), O.forward(og(g), f)) <= TOL
+    assert rel(run_adj(plan, d, cuda_dev), O.adjoint(og(g), d)) <= TOL
+
+
+@pytest.mark.parametrize("g", [
+    Geometry(8, 1, 0.0, 2 * math.pi, 1, 2.0, 3),        # smallest everything
+    Geometry(8, 3, 1.0, 0.1, 5, 0.3, 4),                # tiny arc, short time range
+    Geometry(12, 7, -2.0, 2 * math.pi, 33, 3.0, 9),     # radii reach beyond the image
+    Geometry(64, 5, 0.7, 0.5 * math.pi, 17, 2.0, 1000), # K much larger than the radii count
+    Geometry(100, 33, 0.0, 2 * math.pi, 150, 2.0, 31),  # N not a multiple of the tiles
+])
+def test_edge_geometries(cuda_dev, g):
+    f = f32(inputs.random_image(g.n, seed=6))
+    d = f32(inputs.random_data(g.n_det, g.n_t, seed=7))
+    plan = PatPlan(g, device=cuda_dev)
+    assert rel(run_fwd(plan, f, cuda_dev), O.forward(og(g), f)) <= TOL
+    assert rel(run_adj(plan, d, cuda_dev), O.adjoint(og(g), d)) <= TOL
+
+
+def test_adjoint_identity_gpu(cuda_dev):
+    g = Geometry(96, 40, 0.2, 1.5 * math.pi, 128, 2.0, 150)
+    plan = PatPlan(g, device=cuda_dev)
+    f = torch.tensor(inputs.random_image(96, seed=8), dtype=torch.float32, device=cuda_dev)
+    d = torch.tensor(inputs.random_data(g.n_det, g.n_t, seed=9), dtype=torch.float32, device=cuda_dev)
+    Af = plan.forward(f)
+    Atd = plan.adjoint(d)
+    lhs = float((Af.double() * d.double()).sum())
+    rhs = float((f.double() * Atd.double()).sum())
+    assert abs(lhs - rhs) <= TOL * float(Af.double().norm() * d.double().norm())
+
+
+def test_uneven_batch_and_identical_batch(cuda_dev):
+    geoms = [Geometry(32, 16, 0.0, 2 * math.pi, 64, 2.0, 64),
+             Geometry(48, 9, 0.5, 0.5 * math.pi, 40, 2.0, 96),
+             Geometry(24, 30, 1.0, 1.5 * math.pi, 100, 2.5, 48),
+             Geometry(32, 16, 0.0, 2 * math.pi, 64, 2.0, 64)]
+    plan = PatPlan(geoms, device=cuda_dev)
+    fo, go = plan.layout()
+    imgs = [f32(inputs.random_image(gg.n, seed=10 + i)) for i, gg in enumerate(geoms)]
+    datas = [f32(inputs.random_data(gg.n_det, gg.n_t, seed=20 + i)) for i, gg in enumerate(geoms)]
+    flat_f = np.concatenate([x.ravel() for x in imgs])
+    flat_g = np.concatenate([x.ravel() for x in datas])
+    out_g = run_fwd(plan, flat_f, cuda_dev)
+    out_f = run_adj(plan, flat_g, cuda_dev)
+    for i, gg in enumerate(geoms):
+        assert rel(out_g[go[i]:go[i + 1]].reshape(gg.n_det, gg.n_t), O.forward(og(gg), imgs[i])) <= TOL
+        assert rel(out_f[fo[i]:fo[i + 1]].reshape(gg.n, gg.n), O.adjoint(og(gg), datas[i])) <= TOL
+    # B identical instances: (B, N, N) -> (B, n_det, n_t)
+    g = geoms[1]
+    bplan = PatPlan([g] * 3, device=cuda_dev)
+    fb = np.stack([f32(inputs.random_image(g.n, seed=30 + i)) for i in range(3)])
+    ob = run_fwd(bplan, fb, cuda_dev)
+    assert ob.shape == (3, g.n_det, g.n_t)
+    for i in range(3):
+        assert rel(ob[i], O.forward(og(g), fb[i])) <= TOL
+
+
+def test_bf16_storage_bounds(cuda_dev):
+    g = Geometry(128, 64, 0.0, 1.5 * math.pi, 256, 2.0, 256)
+    f = inputs.mixed_phantom(128, 12, 5, seed=11)
+    fb = torch.tensor(f, dtype=torch.bfloat16)
+    f_b = fb.double().numpy()
+    plan = PatPlan(g, device=cuda_dev, image_dtype=torch.bfloat16)
+    out = plan.forward(fb.to(cuda_dev))
+    torch.cuda.synchronize()
+    out = out.double().cpu().numpy()
+    assert rel(out, O.forward(og(g), f_b)) <= TOL
+    assert rel(out, O.forward(og(g), f)) <= 4e-3
+    d = f32(inputs.random_data(g.n_det, g.n_t, seed=12))
+    fa = plan.adjoint(torch.tensor(d, dtype=torch.float32, device=cuda_dev))
+    torch.cuda.synchronize()
+    assert fa.dtype == torch.bfloat16
+    assert rel(fa.double().cpu().numpy(), O.adjoint(og(g), d)) <= 4e-3
+
+
+def test_tv_value_and_gradient(cuda_dev):
+    g = Geometry(72, 8, 0.0, math.pi, 16, 2.0, 16)
+    plan = PatPlan([g, g], device=cuda_dev)
+    f = np.stack([f32(inputs.vessel_phantom(72, 6, seed=13)), f32(inputs.random_image(72, seed=14))])
+    val, grad = plan.tv_grad(torch.tensor(f, dtype=torch.float32, device=cuda_dev), 1e-2)
+    torch.cuda.synchronize()
+    for i in range(2):
+        rv, rg = O.tv(f[i], 1e-2)
+        assert abs(float(val[i]) - rv) <= 1e-5 * rv
+        assert rel(grad[i].double().cpu().numpy(), rg) <= 1e-5
+
+
+def test_residual_and_descent_step(cuda_dev):
+    g = Geometry(40, 10, 0.0, math.pi, 20, 2.0, 16)
+    plan = PatPlan(g, device=cuda_dev)
+    a = torch.randn(10, 20, device=cuda_dev)
+    b = torch.randn(10, 20, device=cuda_dev)
+    r = plan.residual(a, b, scale=2.0)
+    assert torch.allclose(r, 2.0 * (a - b), rtol=1e-6, atol=1e-6)
+    f = torch.rand(40, 40, device=cuda_dev) - 0.3
+    adj = torch.randn(40, 40, device=cuda_dev)
+    tvg = torch.randn(40, 40, device=cuda_dev)
+    delta = torch.zeros(2, device=cuda_dev)
+    f0 = f.clone()
+    plan.descent_step(f, adj, tvg, tau=0.1, lam=0.5, nonneg=True, delta=delta)
+    ref = torch.clamp(f0 - 0.1 * (adj + 0.5 * tvg), min=0)
+    assert torch.allclose(f, ref, rtol=1e-6, atol=1e-6)
+    assert abs(float(delta[0]) - float(((ref - f0) ** 2).sum())) <= 1e-4 * float(((ref - f0) ** 2).sum())
+    assert abs(float(delta[1]) - float((ref ** 2).sum())) <= 1e-4 * float((ref ** 2).sum())
+
+
+def test_deterministic_and_sample_count(cuda_dev):
+    g = vessel256_half().geometries[0]
+    plan = PatPlan(g, device=cuda_dev)
+    f = torch.tensor(inputs.random_image(256, seed=15), dtype=torch.float32, device=cuda_dev)
+    d = torch.tensor(inputs.random_data(g.n_det, g.n_t, seed=16), dtype=torch.float32, device=cuda_dev)
+    a1, a2 = plan.forward(f), plan.forward(f).clone()
+    b1, b2 = plan.adjoint(d), plan.adjoint(d).clone()
+    assert torch.equal(a1, a2) and torch.equal(b1, b2)
+    info = plan.info()
+    ref = O.count_samples(og(g))
+    assert abs(info["samples"] - ref) <= 1e-4 * ref
+    assert info["sample_slots"] >= info["samples"]
+
+
+def test_plan_errors(cuda_dev):
+    from paper_2604_19176_gb300._lib import PatError
+    with pytest.raises(PatError):
+        PatPlan(Geometry(10, 4, 0.0, math.pi, 8, 2.0, 8), device=cuda_dev)   # N not a multiple of 4
+    with pytest.raises(PatError):
+        PatPlan(Geometry(16, 4, 0.0, 7.0, 8, 2.0, 8), device=cuda_dev)    # arc beyond 2 pi
+    plan = PatPlan(Geometry(16, 4, 0.0, math.pi, 8, 2.0, 8), device=cuda_dev)
+    with pytest.raises(ValueError):
+        plan.forward(torch.zeros(15, 16, device=cuda_dev))
+    plan.close()
