@@ -130,8 +130,8 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
     if (opt.q_piece == 0) opt.q_piece = 128;
     if (opt.q_piece < 4 || opt.q_piece % 4 != 0) return PAT_ERR_INVALID_ARG;
     if (opt.band_rows != 0 && (opt.band_rows < 3 || opt.band_rows > 8192)) return PAT_ERR_INVALID_ARG;
-    if (opt.adj_groups == 0) opt.adj_groups = 4;
-    if (opt.adj_groups != 1 && opt.adj_groups != 2 && opt.adj_groups != 4) return PAT_ERR_INVALID_ARG;
+    if (opt.adj_groups < 0 || opt.adj_groups > 16) return PAT_ERR_INVALID_ARG;
+    if (opt.adj_mode < 0 || opt.adj_mode > 2) return PAT_ERR_INVALID_ARG;
     const bool bf16 = opt.image_dtype == PAT_BF16;
     for (int i = 0; i < n_instances; ++i)
         if (!valid_geometry(geoms[i], bf16)) return PAT_ERR_INVALID_ARG;
@@ -277,7 +277,9 @@ pat_status_t pat_plan_sync_status(pat_plan_t h, void* stream)
         return PAT_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
     if (word == 0) return PAT_OK;
+    // a launch that gave up may have left counters armed: clear them with the word
     if (cudaMemsetAsync(p->dp.status, 0, sizeof(int32_t), st) != cudaSuccess) return PAT_ERR_CUDA;
+    if (cudaMemsetAsync(p->d_counters, 0, p->counters_bytes, st) != cudaSuccess) return PAT_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
     return PAT_ERR_TIMEOUT;
 }

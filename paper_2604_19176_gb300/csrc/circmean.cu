@@ -1,0 +1,240 @@
+// circmean.cu — forward circular means M = C f (the first stage of A).
+//
+// M[j][m] = sum_q f~(y_j + r_m (cos phi_q, sin phi_q)) (the 1/K of the
+// trapezoid rule is applied by the Abel stage), f~ the bilinear interpolant
+// of f with zero outside the grid: the circular mean of the 2D Poisson
+// formula for the wave problem Eq. (1)-(2), discretised as in include/pat.h.
+//
+// Persistent CTAs.  CTA c owns segments cta_seg[c] .. cta_seg[c+1]-1.  For
+// each it stages the segment's image band (TMA bulk copies, one per image
+// row, completing on an mbarrier) and the segment's unit list in shared
+// memory; then its warps take units in order (largest first) from a shared
+// counter.  Lane l of a warp handles radius m0 + l % ML and angles
+// q0 + l / ML + i * (32 / ML); lanes walk along rays, so their 2 x 2 texel
+// reads are spatially coherent.  Each unit writes its own partial-sum slot,
+// so the result does not depend on scheduling.
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace patgpu {
+
+namespace {
+
+// One bilinear sample of the staged band; 0 for samples whose cell lies
+// outside the band (they belong to another band or to no pixel).
+template <typename T>
+__device__ __forceinline__ float sample(const T* __restrict__ s, int W, float rho, float2 cs, float U, float V,
+                                        float ulo, float uhi, float vlo, float vhi)
+{
+    const float u = __fmaf_rn(rho, cs.x, U);
+    const float v = __fmaf_rn(rho, cs.y, V);
+    const float fu = floorf(u), fv = floorf(v);
+    const bool ok = (fu >= ulo) & (fu <= uhi) & (fv >= vlo) & (fv <= vhi);
+    const float a = __fsub_rn(u, fu), b = __fsub_rn(v, fv);
+    const T* p = s + (__float2int_rz(fv) * W + __float2int_rz(fu));
+    float f00 = 0.f, f10 = 0.f, f01 = 0.f, f11 = 0.f;
+    if (ok) {
+        f00 = ld_img(p);
+        f10 = ld_img(p + 1);
+        f01 = ld_img(p + W);
+        f11 = ld_img(p + W + 1);
+    }
+    const float top = fmaf(a, f10 - f00, f00);
+    const float bot = fmaf(a, f11 - f01, f01);
+    return fmaf(b, bot - top, top);
+}
+
+} // namespace
+
+template <int ML, typename T>
+__global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* __restrict__ f)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_next;
+    Unit* su = reinterpret_cast<Unit*>(smem_raw);
+    T* s = reinterpret_cast<T*>(smem_raw + kMaxSegUnits * sizeof(Unit));
+    constexpr int QL = kWarp / ML;
+    constexpr int CO = ImgTraits<T>::col_off;
+    const int lane = threadIdx.x & 31;
+    const int ml = lane % ML, ql = lane / ML;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t parity = 0;
+    const int seg_begin = dp.cta_seg[blockIdx.x], seg_end = dp.cta_seg[blockIdx.x + 1];
+    for (int sidx = seg_begin; sidx < seg_end; ++sidx) {
+        const Segment sg = dp.segs[sidx];
+        const InstDev in = dp.inst[sg.inst];
+        const int n = in.n;
+        const int W = ImgTraits<T>::pitch(n);
+        const int rows = sg.band_hi - sg.band_lo + 1;
+        const int nu = sg.unit_end - sg.unit_begin;
+        __syncthreads(); // every warp is done with the previous band and units
+
+        // ---- stage band rows and units (TMA bulk copies) -----------------
+        if (threadIdx.x < 32) {
+            const int r0 = max(sg.band_lo, 0), r1 = min(sg.band_hi, n - 1);
+            const uint32_t row_bytes = (uint32_t)n * sizeof(T);
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                const uint32_t total =
+                    (r1 >= r0 ? (uint32_t)(r1 - r0 + 1) * row_bytes : 0u) + (uint32_t)nu * (uint32_t)sizeof(Unit);
+                mbar_arrive_expect_tx(&bar, total);
+                s_next = 0;
+            }
+            __syncwarp();
+            for (int r = r0 + lane; r <= r1; r += 32)
+                bulk_g2s(s + (r - sg.band_lo) * W + CO, f + in.f_off + (size_t)r * n, row_bytes, &bar);
+            if (lane == 0 && nu > 0)
+                bulk_g2s(su, dp.units + sg.unit_begin, (uint32_t)nu * (uint32_t)sizeof(Unit), &bar);
+        }
+        // ---- zero borders: columns -1 and N.. (pad), rows outside the image
+        const T zero = T(0.f);
+        const int pad = W - (CO + n);
+        for (int i = threadIdx.x; i < rows * (pad + 1); i += blockDim.x) {
+            const int ri = i / (pad + 1), c = i - ri * (pad + 1);
+            s[ri * W + (c == 0 ? CO - 1 : CO + n + c - 1)] = zero;
+        }
+        for (int ri = 0; ri < rows; ++ri) {
+            const int r = sg.band_lo + ri;
+            if (r >= 0 && r < n) continue;
+            for (int c = threadIdx.x; c < n; c += blockDim.x) s[ri * W + CO + c] = zero;
+        }
+        __syncthreads();
+        if (!mbar_wait_bounded(&bar, parity, dp.status, 1)) {
+            mbar_wait_bounded(&bar, parity, dp.status, 1); // let copies in flight land before exiting
+            return;
+        }
+        parity ^= 1u;
+
+        // ---- units --------------------------------------------------------
+        // cell (i0c, j0c) in centred units lives at s[j0c * W + i0c + base]
+        const T* sb = s + ((in.c0 - sg.band_lo) * W + in.c0 + CO);
+        const float ulo = (float)(-1 - in.c0), uhi = (float)(n - 1 - in.c0);
+        const float vlo = (float)(sg.band_lo - in.c0), vhi = (float)(sg.band_hi - 1 - in.c0);
+        const float* detU = dp.detU + in.det_off;
+        const float* detV = dp.detV + in.det_off;
+        const float2* trig = dp.trig + in.trig_off;
+
+        for (;;) {
+            int u = 0;
+            if (lane == 0) u = atomicAdd(&s_next, 1);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (u >= nu) break;
+            const Unit un = su[u];
+            const int m = un.m0 + ml;
+            const float rho = (float)m * in.delta;
+            const float U = __ldg(detU + un.j), V = __ldg(detV + un.j);
+            const float2* tq = trig + un.q0 + ql;
+            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+            int i = ql;
+            for (; i + 3 * QL < un.nq; i += 4 * QL, tq += 4 * QL) {
+                const float2 c0 = __ldg(tq), c1 = __ldg(tq + QL), c2 = __ldg(tq + 2 * QL), c3 = __ldg(tq + 3 * QL);
+                acc0 += sample(sb, W, rho, c0, U, V, ulo, uhi, vlo, vhi);
+                acc1 += sample(sb, W, rho, c1, U, V, ulo, uhi, vlo, vhi);
+                acc2 += sample(sb, W, rho, c2, U, V, ulo, uhi, vlo, vhi);
+                acc3 += sample(sb, W, rho, c3, U, V, ulo, uhi, vlo, vhi);
+            }
+            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(sb, W, rho, __ldg(tq), U, V, ulo, uhi, vlo, vhi);
+            float acc = (acc0 + acc1) + (acc2 + acc3);
+#pragma unroll
+            for (int o = ML; o < kWarp; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            const size_t plane = (size_t)in.n_det * in.n_r;
+            float* slots = dp.mpart + in.mpart_off + (size_t)un.j * in.n_r;
+            if (ql == 0 && m < in.n_r) slots[(size_t)un.slot * plane + m] = acc;
+            // The last unit of (j, radius block) to finish sums the block's slots in
+            // slot order (deterministic) into M and re-arms the counter.
+            __threadfence();
+            const int blk = un.j * in.nmb + un.m0 / ML;
+            const int total = reinterpret_cast<const int32_t*>(dp.slotcnt + in.slotcnt_off)[blk];
+            int last = 0;
+            if (lane == 0) last = (atomicAdd(dp.slot_arrivals + in.arrive_off + blk, 1) == total - 1);
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                if (ql == 0 && m < in.n_r) {
+                    float s = 0.f;
+                    for (int sl = 0; sl < total; ++sl) s += __ldcg(slots + (size_t)sl * plane + m);
+                    dp.msum[in.mbar_off + (size_t)un.j * in.n_r + m] = s;
+                }
+                if (lane == 0) dp.slot_arrivals[in.arrive_off + blk] = 0;
+            }
+        }
+    }
+}
+
+// Samples whose cell touches the grid, counted with the kernels' FP32 arithmetic.
+__global__ void k_count_samples(DevPlan dp, int inst_idx, unsigned long long* __restrict__ out)
+{
+    const InstDev in = dp.inst[inst_idx];
+    const int j = blockIdx.x;
+    const float U = dp.detU[in.det_off + j], V = dp.detV[in.det_off + j];
+    const float2* trig = dp.trig + in.trig_off;
+    const float lo = (float)(-1 - in.c0), hi = (float)(in.n - 1 - in.c0);
+    unsigned long long c = 0;
+    for (int m = threadIdx.x; m < in.n_r; m += blockDim.x) {
+        const float rho = (float)m * in.delta;
+        for (int q = 0; q < in.K; ++q) {
+            const float2 cs = trig[q];
+            const float fu = floorf(__fmaf_rn(rho, cs.x, U)), fv = floorf(__fmaf_rn(rho, cs.y, V));
+            c += (fu >= lo && fu <= hi && fv >= lo && fv <= hi) ? 1ull : 0ull;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
+
+// ---------------------------------------------------------------------------
+namespace {
+template <int ML, typename T>
+const void* circ_fn()
+{
+    return reinterpret_cast<const void*>(k_circmean<ML, T>);
+}
+const void* circ_select(int ml, bool bf16)
+{
+    if (bf16) return ml == 16 ? circ_fn<16, __nv_bfloat16>() : ml == 8 ? circ_fn<8, __nv_bfloat16>()
+                                                                           : circ_fn<32, __nv_bfloat16>();
+    return ml == 16 ? circ_fn<16, float>() : ml == 8 ? circ_fn<8, float>() : circ_fn<32, float>();
+}
+} // namespace
+
+cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st)
+{
+    if (dp.n_fwd_ctas == 0) return cudaSuccess;
+    const void* fn = circ_select(dp.m_lanes, dp.bf16 != 0);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dp.fwd_smem_bytes);
+    if (e != cudaSuccess) return e;
+    DevPlan copy = dp;
+    const void* fptr = f;
+    void* args[] = {&copy, &fptr};
+    return cudaLaunchKernel(fn, dim3(dp.n_fwd_ctas), dim3(kCircThreads), args, (size_t)dp.fwd_smem_bytes, st);
+}
+
+int circmean_blocks_per_sm(int m_lanes, bool bf16, int smem_bytes)
+{
+    const void* fn = circ_select(m_lanes, bf16);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kCircThreads, smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_count_samples(const DevPlan& dp, int inst_idx, int n_det, unsigned long long* out, cudaStream_t st)
+{
+    k_count_samples<<<n_det, 128, 0, st>>>(dp, inst_idx, out);
+    return cudaGetLastError();
+}
+
+} // namespace patgpu

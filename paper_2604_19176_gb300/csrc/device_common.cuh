@@ -1,0 +1,158 @@
+// device_common.cuh — small device helpers shared by the kernels of this
+// library (shared-memory band layout, TMA bulk copies with mbarriers,
+// bounded waits, reductions, the polynomial atan2 of the adjoint window).
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "pat_internal.h"
+
+namespace patgpu {
+
+__device__ __forceinline__ float ld_img(const float* p) { return *p; }
+__device__ __forceinline__ float ld_img(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ int pitch_f32(int n)
+{
+    int w = n + kColOff + 1;
+    return w + ((12 - (w & 31)) & 31);
+}
+__device__ __forceinline__ int pitch_bf16(int n)
+{
+    int w = n + kColOffBF16 + 1;
+    return w + ((24 - (w & 63)) & 63);
+}
+
+template <typename T> struct ImgTraits;
+template <> struct ImgTraits<float> {
+    static __device__ __forceinline__ int pitch(int n) { return pitch_f32(n); }
+    static constexpr int col_off = kColOff;
+};
+template <> struct ImgTraits<__nv_bfloat16> {
+    static __device__ __forceinline__ int pitch(int n) { return pitch_bf16(n); }
+    static constexpr int col_off = kColOffBF16;
+};
+
+// ---------------------------------------------------------------------------
+// TMA (bulk async copy) and mbarrier wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier, giving up after ~limit_cycles SM
+// clocks; on give-up records `code` in the device status word and returns
+// false (the caller must then not use the data the barrier guards).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int32_t* status, int32_t code,
+                                                  long long limit_cycles = 2000000000LL)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit_cycles) {
+            if (status) atomicExch(status, code);
+            return false;
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Angular window of the adjoint gather
+// ---------------------------------------------------------------------------
+constexpr float kPi = 3.14159265358979f;
+
+// atan(x) on [0, 1]: odd polynomial x * p(x^2), coefficients fitted by
+// iteratively reweighted least squares on 4000 Chebyshev nodes; evaluated in
+// FP32 its max abs error is 1.7e-6 rad.  Only the adjoint's candidate window
+// uses it (widened by a margin) and every candidate is re-checked exactly.
+__device__ __forceinline__ float atan_01(float x)
+{
+    const float x2 = x * x;
+    float p = -0.01171913f;
+    p = fmaf(p, x2, 0.05264734f);
+    p = fmaf(p, x2, -0.11642648f);
+    p = fmaf(p, x2, 0.19354038f);
+    p = fmaf(p, x2, -0.33262283f);
+    p = fmaf(p, x2, 0.99997722f);
+    return x * p;
+}
+
+__device__ __forceinline__ float atan2_approx(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    float r = atan_01(t);
+    if (ay > ax) r = 0.5f * kPi - r;
+    if (x < 0.f) r = kPi - r;
+    return copysignf(r, y);
+}
+
+// Upper bound of asin(s), s in [0, 1]: s (1 + s^2/4) >= asin(s) for s <= 0.7.
+__device__ __forceinline__ float asin_upper(float s)
+{
+    return s <= 0.7f ? s * fmaf(0.25f, s * s, 1.0f) : asinf(fminf(s, 1.0f)) + 1e-6f;
+}
+
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+} // namespace patgpu

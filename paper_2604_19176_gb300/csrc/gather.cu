@@ -1,0 +1,277 @@
+// gather.cu — adjoint circular means f = C^T Mbar as a gather over pixels.
+//
+// C^T scatters every sample's bilinear weights; here every output is instead
+// summed by the one warp or thread that owns it, in a fixed order (no atomics,
+// deterministic).  Work happens per cell [cx, cx+1) x [cy, cy+1): a sample
+// that lands in the cell adds w (1-a)(1-b), w a(1-b), w (1-a)b, w ab to the
+// cell's four corner sums Z (w = Mbar[j][m]); pixel (px, py) then sums
+// Z00(px,py) + Z10(px-1,py) + Z01(px,py-1) + Z11(px-1,py-1) (times 1/K).
+//
+// Finding a cell's samples.  For each detector, a cell can only receive
+// samples from rays q whose direction passes within R = sqrt(2)/2 (+ margin)
+// of its centre; each such ray is intersected with the cell (slab test,
+// widened by a margin that covers FP32 rounding) to get the run of radii m
+// that can land in it, and each candidate is re-evaluated with exactly the
+// forward's FP32 expression.  Hits come out in the order (j, q, m).
+//
+// Two ways to run this:
+//   list mode (default when the codes fit): at plan creation the enumeration
+//     runs twice (count, then fill) to store every cell's hits as packed
+//     (j, m, q) codes; each call is then a warp-per-cell gather over that
+//     list that recomputes the weights from the codes.
+//   compute mode: the enumeration runs on every call (k_adj_cells), one warp
+//     per 8 x 4 patch of cells and detector group, partial Z per group.
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace patgpu {
+
+namespace {
+constexpr float kRcell = 0.70710678f + 0.004f;  // half cell diagonal + rounding margin (pixels)
+constexpr float kSlabEps = 0.01f;                // slab widening (pixels)
+constexpr float kAngMargin = 1.0e-5f;            // > 5x the atan2_approx error (radians)
+
+// Calls hit(j, m, q, u, v) for every sample (j in j0, j0 + dj, ...) that
+// lands in centred cell (cxf, cyf), in (j, q, m) order; q in [0, K).
+template <typename Hit>
+__device__ __forceinline__ void enumerate_cell(const DevPlan& dp, const InstDev& in, float cxf, float cyf, int j0,
+                                               int dj, Hit&& hit)
+{
+    const float ccx = cxf + 0.5f, ccy = cyf + 0.5f;
+    const float* detU = dp.detU + in.det_off;
+    const float* detV = dp.detV + in.det_off;
+    const float2* trig = dp.trig + in.trig_off;
+    const float2* rtrig = dp.rtrig + in.rtrig_off;
+    const int K = in.K;
+    const float delta = in.delta;
+    for (int j = j0; j < in.n_det; j += dj) {
+        const float U = __ldg(detU + j), V = __ldg(detV + j);
+        const float du = ccx - U, dv = ccy - V;
+        const float rc = sqrtf(fmaf(du, du, dv * dv));
+        const int mlo = max(0, (int)ceilf((rc - kRcell) * in.inv_delta));
+        const int mhi = min(in.n_r - 1, (int)floorf((rc + kRcell) * in.inv_delta));
+        if (mlo > mhi) continue;
+        int qlo = 0, qn = K;
+        if (rc > 1.25f * kRcell) {
+            const float phic = atan2_approx(dv, du);
+            const float alpha = asin_upper(__fdividef(kRcell, rc)) + kAngMargin;
+            qlo = (int)ceilf((phic - alpha) * in.inv_dphi);
+            qn = min((int)floorf((phic + alpha) * in.inv_dphi) - qlo + 1, K);
+            if (qlo < 0) qlo += K;
+        }
+        const float ax0 = (cxf - kSlabEps) - U, ax1 = (cxf + 1.f + kSlabEps) - U;
+        const float ay0 = (cyf - kSlabEps) - V, ay1 = (cyf + 1.f + kSlabEps) - V;
+        for (int i = 0; i < qn; ++i) {
+            const int q = qlo + i;
+            const float2 ri = __ldg(rtrig + q);
+            const float tx0 = ax0 * ri.x, tx1 = ax1 * ri.x;
+            const float ty0 = ay0 * ri.y, ty1 = ay1 * ri.y;
+            const float lo = fmaxf(fminf(tx0, tx1), fminf(ty0, ty1));
+            const float hi = fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1));
+            const int m0 = max(mlo, (int)ceilf(lo));
+            const int m1 = min(mhi, (int)floorf(hi));
+            if (m0 > m1) continue;
+            const float2 cs = __ldg(trig + q);
+            for (int m = m0; m <= m1; ++m) {
+                const float rho = (float)m * delta;
+                const float u = __fmaf_rn(rho, cs.x, U);
+                const float v = __fmaf_rn(rho, cs.y, V);
+                if (floorf(u) == cxf && floorf(v) == cyf) hit(j, m, q >= K ? q - K : q, u, v);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void add_corners(float4& z, float a, float b, float w)
+{
+    const float wb = w * b, w1 = w - wb; // w b, w (1 - b)
+    z.y = fmaf(a, w1, z.y);              // Z10 += w a (1 - b)
+    z.x = fmaf(-a, w1, z.x + w1);        // Z00 += w (1 - a)(1 - b)
+    z.w = fmaf(a, wb, z.w);              // Z11 += w a b
+    z.z = fmaf(-a, wb, z.z + wb);        // Z01 += w (1 - a) b
+}
+
+__device__ __forceinline__ int take_item(int32_t* ctr, int lane)
+{
+    int item = 0;
+    if (lane == 0) item = atomicAdd(ctr, 1);
+    return __shfl_sync(0xffffffffu, item, 0);
+}
+
+// the last warp to run out of items re-arms the queue for the next launch
+__device__ __forceinline__ void release_queue(int32_t* ctr, int lane)
+{
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    if (lane == 0 && atomicAdd(ctr + 1, 1) == nwarps - 1) {
+        ctr[0] = 0;
+        ctr[1] = 0;
+    }
+}
+} // namespace
+
+// ---------------------------------------------------------------------------
+// Compute mode: one warp per (8 x 4 cell patch, detector group); dynamic
+// queue over items sorted by estimated cost.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 5) k_adj_cells(DevPlan dp)
+{
+    const int lane = threadIdx.x & 31;
+    const int G = dp.adj_groups;
+    for (;;) {
+        const int item = take_item(dp.work_counters, lane);
+        if (item >= dp.n_cell_items) break;
+        const CellItem it = dp.cell_items[item];
+        const InstDev in = dp.inst[it.inst];
+        const int n = in.n;
+        const int cx = it.x0 + (lane & (kPatchW - 1)), cy = it.y0 + lane / kPatchW;
+        if (cx > n - 1 || cy > n - 1) continue;
+        const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
+        const float* mb = dp.mbar + in.mbar_off;
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        enumerate_cell(dp, in, cxf, cyf, it.group, G, [&](int j, int m, int, float u, float v) {
+            add_corners(z, __fsub_rn(u, cxf), __fsub_rn(v, cyf), __ldg(mb + (size_t)j * in.n_r + m));
+        });
+        dp.zbuf[in.z_off + (size_t)it.group * (n + 1) * (n + 1) + (size_t)(cy + 1) * (n + 1) + (cx + 1)] = z;
+    }
+    release_queue(dp.work_counters, lane);
+}
+
+// ---------------------------------------------------------------------------
+// List building (plan creation): count, then fill, the hits of every cell of
+// instance `inst_idx`, all detectors, in enumeration order.  Thread = cell.
+// ---------------------------------------------------------------------------
+template <int FILL>
+__global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int32_t* __restrict__ counts,
+                                                   const int64_t* __restrict__ offs, uint32_t* __restrict__ codes)
+{
+    const InstDev in = dp.inst[inst_idx];
+    const int n = in.n, w = n + 1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= w * w) return;
+    const int cx = idx % w - 1, cy = idx / w - 1;
+    const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
+    int64_t k = FILL ? offs[idx] : 0;
+    const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
+    enumerate_cell(dp, in, cxf, cyf, 0, 1, [&](int j, int m, int q, float, float) {
+        if (FILL) codes[k] = ((uint32_t)j << mbq) | ((uint32_t)m << qb) | (uint32_t)q;
+        ++k;
+    });
+    if (!FILL) counts[idx] = (int32_t)k;
+}
+
+// ---------------------------------------------------------------------------
+// List mode: one warp per cell (queue sorted by list length); lanes stride the
+// cell's codes, recompute each sample exactly as the forward does, and the
+// four corner sums are reduced across the warp in a fixed tree.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        const int item = take_item(dp.work_counters + 2, lane);
+        if (item >= dp.n_list_items) break;
+        const int2 li = dp.list_items[item]; // (instance, cell index)
+        const InstDev in = dp.inst[li.x];
+        const int w = in.n + 1;
+        const float cxf = (float)(li.y % w - 1 - in.c0), cyf = (float)(li.y / w - 1 - in.c0);
+        const int64_t* off = dp.cell_off + in.list_off;
+        const int64_t beg = off[li.y], end = off[li.y + 1];
+        const float* detU = dp.detU + in.det_off;
+        const float* detV = dp.detV + in.det_off;
+        const float2* trig = dp.trig + in.trig_off;
+        const float* mb = dp.mbar + in.mbar_off;
+        const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
+        const uint32_t qmask = (1u << qb) - 1u, mmask = (1u << in.code_mbits) - 1u;
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t k = beg + lane; k < end; k += kWarp) {
+            const uint32_t code = __ldg(dp.codes + k);
+            const int j = (int)(code >> mbq), m = (int)((code >> qb) & mmask), q = (int)(code & qmask);
+            const float2 cs = __ldg(trig + q);
+            const float rho = (float)m * in.delta;
+            const float u = __fmaf_rn(rho, cs.x, __ldg(detU + j));
+            const float v = __fmaf_rn(rho, cs.y, __ldg(detV + j));
+            // the sample lies in this cell, so floor(u) == cxf: a = u - floor(u)
+            add_corners(z, __fsub_rn(u, cxf), __fsub_rn(v, cyf), __ldg(mb + (size_t)j * in.n_r + m));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
+            z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
+            z.z += __shfl_xor_sync(0xffffffffu, z.z, o);
+            z.w += __shfl_xor_sync(0xffffffffu, z.w, o);
+        }
+        if (lane == 0) dp.zbuf[in.z_off + li.y] = z;
+    }
+    release_queue(dp.work_counters + 2, lane);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_combine(DevPlan dp, T* __restrict__ fout)
+{
+    const ImgTile t = dp.img_tiles[blockIdx.x];
+    const InstDev in = dp.inst[t.inst];
+    const int n = in.n;
+    const int px = t.x0 + (threadIdx.x & 31), py = t.y0 + (threadIdx.x >> 5);
+    if (px >= n || py >= n) return;
+    const int w = n + 1;
+    const float4* z = dp.zbuf + in.z_off;
+    const int groups = dp.adj_mode == 1 ? 1 : dp.adj_groups;
+    float s = 0.f;
+    for (int g = 0; g < groups; ++g) {
+        const float4* zg = z + (size_t)g * w * w;
+        // cell (cx, cy) is stored at (cy + 1) * w + (cx + 1)
+        s += __ldg(&zg[(size_t)(py + 1) * w + px + 1].x) + __ldg(&zg[(size_t)(py + 1) * w + px].y) +
+             __ldg(&zg[(size_t)py * w + px + 1].z) + __ldg(&zg[(size_t)py * w + px].w);
+    }
+    const float val = s * in.inv_K;
+    if constexpr (sizeof(T) == 4) fout[in.f_off + (size_t)py * n + px] = val;
+    else fout[in.f_off + (size_t)py * n + px] = __float2bfloat16(val);
+}
+
+int adj_cells_blocks_per_sm()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_cells, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+int adj_list_blocks_per_sm()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_list, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* offs,
+                             uint32_t* codes, cudaStream_t st)
+{
+    const int cells = (n + 1) * (n + 1);
+    const int blocks = (cells + 255) / 256;
+    if (codes) k_adj_build<1><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, codes);
+    else k_adj_build<0><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, codes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_gather(const DevPlan& dp, void* f, cudaStream_t st)
+{
+    if (dp.adj_mode == 1) {
+        if (dp.n_list_items == 0) return cudaSuccess;
+        k_adj_list<<<dp.cell_blocks, 256, 0, st>>>(dp);
+    } else {
+        if (dp.n_cell_items == 0) return cudaSuccess;
+        k_adj_cells<<<dp.cell_blocks, 256, 0, st>>>(dp);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (dp.bf16) k_adj_combine<__nv_bfloat16><<<dp.n_img_tiles, 256, 0, st>>>(dp, static_cast<__nv_bfloat16*>(f));
+    else k_adj_combine<float><<<dp.n_img_tiles, 256, 0, st>>>(dp, static_cast<float*>(f));
+    return cudaGetLastError();
+}
+
+} // namespace patgpu

@@ -21,7 +21,16 @@ cudaError_t launch_descent(const DevPlan& dp, float* f, const float* adj, const 
 cudaError_t launch_count_samples(const DevPlan& dp, int inst_idx, int n_det, unsigned long long* out,
                                  cudaStream_t st);
 
-// Occupancy of the circular-mean kernel for the plan's tile shape.
+// Occupancy of the circular-mean kernel for the plan's tile shape, and of the
+// adjoint cell kernel (256-thread CTAs).
 int circmean_blocks_per_sm(int m_lanes, bool bf16, int smem_bytes);
+int adj_cells_blocks_per_sm();
+int adj_list_blocks_per_sm();
+
+// Adjoint list building at plan creation: counts (codes == nullptr) or fills
+// (codes != nullptr, offs = exclusive prefix sums of the counts) the sample
+// lists of every cell of instance inst_idx.
+cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* offs,
+                             uint32_t* codes, cudaStream_t st);
 
 } // namespace patgpu

@@ -1,0 +1,132 @@
+// misc.cu — TV value/gradient, data residual and projected descent step.
+//
+// TV(f) = sum_{i,j} sqrt(dx^2 + dy^2 + eps^2) with forward differences
+// (zero on the last column / row): the regulariser of Eq. (4) and Eq. (5).
+// The descent step applies the projection onto f >= 0 of Eq. (4).
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace patgpu {
+
+namespace {
+__device__ __forceinline__ float tv_term(const float* f, int n, int i, int j, float eps2, float& dx, float& dy)
+{
+    const float c = f[(size_t)i * n + j];
+    dx = (j + 1 < n) ? f[(size_t)i * n + j + 1] - c : 0.f;
+    dy = (i + 1 < n) ? f[(size_t)(i + 1) * n + j] - c : 0.f;
+    return sqrtf(fmaf(dx, dx, fmaf(dy, dy, eps2)));
+}
+} // namespace
+
+__global__ void __launch_bounds__(256) k_tv(DevPlan dp, const float* __restrict__ f, float eps, float* __restrict__ grad)
+{
+    __shared__ float red[8];
+    const ImgTile t = dp.img_tiles[blockIdx.x];
+    const InstDev in = dp.inst[t.inst];
+    const int n = in.n;
+    const float* fi = f + in.f_off;
+    const int j = t.x0 + (threadIdx.x & 31), i = t.y0 + (threadIdx.x >> 5);
+    const float eps2 = eps * eps;
+    float val = 0.f;
+    if (i < n && j < n) {
+        float dx, dy;
+        const float s = tv_term(fi, n, i, j, eps2, dx, dy);
+        val = s;
+        if (grad) {
+            float gsum = -(dx + dy) / s;
+            if (j > 0) {
+                float dxl, dyl;
+                const float sl = tv_term(fi, n, i, j - 1, eps2, dxl, dyl);
+                gsum += dxl / sl;
+            }
+            if (i > 0) {
+                float dxu, dyu;
+                const float su = tv_term(fi, n, i - 1, j, eps2, dxu, dyu);
+                gsum += dyu / su;
+            }
+            grad[in.f_off + (size_t)i * n + j] = gsum;
+        }
+    }
+    const float s = block_sum<256>(val, red);
+    if (threadIdx.x == 0) dp.tv_partial[blockIdx.x] = s;
+}
+
+// Per-instance sums of per-tile partials (fixed order): out[i*ncomp + c].
+__global__ void k_tile_sums(DevPlan dp, const float* __restrict__ part, int ncomp, float* __restrict__ out)
+{
+    const int inst = blockIdx.x;
+    if (threadIdx.x >= ncomp) return;
+    float s = 0.f;
+    for (int b = 0; b < dp.n_img_tiles; ++b)
+        if (dp.img_tiles[b].inst == inst) s += part[(size_t)b * ncomp + threadIdx.x];
+    out[(size_t)inst * ncomp + threadIdx.x] = s;
+}
+
+__global__ void k_residual(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ r, float scale,
+                           int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = scale * (a[i] - b[i]);
+}
+
+__global__ void __launch_bounds__(256) k_descent(DevPlan dp, float* __restrict__ f, const float* __restrict__ adj,
+                                                 const float* __restrict__ tvg, float tau, float lam, int nonneg,
+                                                 float* __restrict__ part)
+{
+    __shared__ float red[8];
+    const ImgTile t = dp.img_tiles[blockIdx.x];
+    const InstDev in = dp.inst[t.inst];
+    const int n = in.n;
+    const int j = t.x0 + (threadIdx.x & 31), i = t.y0 + (threadIdx.x >> 5);
+    float d2 = 0.f, n2 = 0.f;
+    if (i < n && j < n) {
+        const size_t idx = in.f_off + (size_t)i * n + j;
+        const float old = f[idx];
+        float gr = adj[idx];
+        if (tvg) gr = fmaf(lam, tvg[idx], gr);
+        float nv = fmaf(-tau, gr, old);
+        if (nonneg) nv = fmaxf(nv, 0.f);
+        f[idx] = nv;
+        d2 = (nv - old) * (nv - old);
+        n2 = nv * nv;
+    }
+    if (part) {
+        const float s0 = block_sum<256>(d2, red);
+        const float s1 = block_sum<256>(n2, red);
+        if (threadIdx.x == 0) {
+            part[2 * blockIdx.x] = s0;
+            part[2 * blockIdx.x + 1] = s1;
+        }
+    }
+}
+
+cudaError_t launch_tv(const DevPlan& dp, const float* f, float eps, float* grad, float* value, cudaStream_t st)
+{
+    if (dp.n_img_tiles == 0) return cudaSuccess;
+    k_tv<<<dp.n_img_tiles, 256, 0, st>>>(dp, f, eps, grad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !value) return e;
+    k_tile_sums<<<dp.n_inst, 32, 0, st>>>(dp, dp.tv_partial, 1, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const float* a, const float* b, float* r, float scale, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256;
+    k_residual<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(a, b, r, scale, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_descent(const DevPlan& dp, float* f, const float* adj, const float* tvg, float tau, float lam,
+                           int nonneg, float* delta, cudaStream_t st)
+{
+    if (dp.n_img_tiles == 0) return cudaSuccess;
+    k_descent<<<dp.n_img_tiles, 256, 0, st>>>(dp, f, adj, tvg, tau, lam, nonneg, delta ? dp.tv_partial : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !delta) return e;
+    k_tile_sums<<<dp.n_inst, 32, 0, st>>>(dp, dp.tv_partial, 2, delta);
+    return cudaGetLastError();
+}
+
+} // namespace patgpu

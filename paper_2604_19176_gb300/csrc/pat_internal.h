@@ -27,8 +27,9 @@ namespace patgpu {
 constexpr int kWarp = 32;
 constexpr int kColOff = 4;        // FP32 shared image: column 0 at word offset 4 (16 B aligned)
 constexpr int kColOffBF16 = 8;    // BF16 shared image: column 0 at element offset 8 (16 B aligned)
-constexpr int kAdjTile = 16;      // adjoint CTA: 16 x 16 cells -> 15 x 15 output pixels
-constexpr int kAdjOut = kAdjTile - 1;
+constexpr int kPatchW = 8;        // adjoint: one warp owns an 8 x 4 patch of cells
+constexpr int kPatchH = 4;
+constexpr int kMaxSegUnits = 256; // circular-mean units staged per segment (shared memory)
 
 // Per-instance descriptor (device resident, read by every kernel).
 struct InstDev {
@@ -40,15 +41,21 @@ struct InstDev {
     int64_t f_off, g_off;          // element offsets of the instance's image / data
     int64_t mpart_off;             // float offset of forward partial slots (n_slots x n_det x n_r)
     int64_t mbar_off;              // float offset of the adjoint's Mbar (n_det x n_r)
-    int64_t p_off;                 // float offset of the Abel matrix (n_t x n_r)
-    int64_t slotcnt_off;           // byte offset of the slot counts (n_det x nmb)
+    int64_t p_off;                 // float offset of the Abel matrix P (n_t x n_r) and of P^T (n_r x n_t)
+    int64_t slotcnt_off;           // byte offset of the slot counts (n_det x nmb int32)
+    int64_t z_off;                 // float4 offset of the adjoint cell sums (groups x (n+1)^2)
+    int64_t rtrig_off;             // float2 offset of (1/(cos_q delta), 1/(sin_q delta)), 2K entries
+    int64_t arrive_off;            // int offset of the slot-arrival counters (n_det x nmb)
+    int64_t list_off;              // adjoint list mode: offset of the (n+1)^2 + 1 cell offsets
+    int32_t code_qbits, code_mbits; // adjoint list mode: code = j << (qb+mb) | m << qb | q
 };
 
 // Circular-mean work unit: radii [m0, m0 + m_lanes) of detector j, angles
 // q0 .. q0 + nq - 1 (mod K), restricted to one image band; its partial sums
-// go to forward slot `slot`.
+// go to forward slot `slot`.  32 bytes so that a segment's units can be
+// bulk-copied to shared memory.
 struct Unit {
-    int32_t j, m0, q0, nq, slot, pad;
+    int32_t j, m0, q0, nq, slot, pad[3];
 };
 
 // A contiguous range of units of one (instance, band), processed by one CTA
@@ -61,18 +68,19 @@ struct Segment {
     int32_t pad[3];
 };
 
-// Output tile of the two Abel (time) stages.
+// Output tile of the two Abel (time) stages: detectors [j0, j0 + kAbelJ),
+// outputs [x0, x0 + kAbelX) (times for the forward, radii for the adjoint).
 struct TimeTile {
-    int32_t inst, j0, x0, pad;     // x0: first time index (forward) or radius index (adjoint)
+    int32_t inst, j0, x0, pad;
 };
 
-// Output tile of the adjoint gather: 16 x 16 cells whose lower-left cell is
-// (x0 - 1, y0 - 1); produces pixels [x0, x0 + 15) x [y0, y0 + 15).
-struct AdjTile {
-    int32_t inst, x0, y0, pad;
+// Adjoint cell item: the 8 x 4 patch of cells with lower-left cell (x0, y0)
+// (absolute indices, >= -1) of instance inst, for detectors j = group (mod G).
+struct CellItem {
+    int32_t inst, x0, y0, group;
 };
 
-// Tile of the elementwise / stencil kernels (TV).
+// Tile of the elementwise / stencil kernels: 32 x 8 pixels.
 struct ImgTile {
     int32_t inst, x0, y0, pad;
 };
@@ -82,28 +90,42 @@ struct DevPlan {
     const InstDev* inst;
     const float* detU;             // U_j (centred pixel units), concatenated per instance
     const float* detV;
-    const float2* trig;            // (cos, sin)(2 pi q / K), concatenated per distinct K
-    const float* P;                // Abel matrices, concatenated per distinct n_t
-    const uint8_t* slotcnt;        // forward slots per (detector, radius block)
+    const float2* trig;            // (cos, sin)(2 pi q / K), 2K entries per distinct K
+    const float2* rtrig;           // per instance: (1/(cos_q delta), 1/(sin_q delta)), 2K entries
+    const float* P;                // Abel matrices P then P^T, per distinct n_t
+    const uint8_t* slotcnt;        // forward slots per (detector, radius block), int32
     const Unit* units;
     const Segment* segs;
     const int32_t* cta_seg;        // CTA c processes segments [cta_seg[c], cta_seg[c+1])
     const TimeTile* fwd_tiles;
     const TimeTile* adj_tiles;
-    const AdjTile* gather_tiles;
+    const CellItem* cell_items;
     const ImgTile* img_tiles;
+    const int64_t* cell_off;       // adjoint list mode: per-cell ranges into codes
+    const uint32_t* codes;         // adjoint list mode: packed (j, m, q) of every sample, by cell
+    const int2* list_items;        // adjoint list mode: (instance, cell), longest lists first
     float* mpart;                  // forward partial slots
+    float* msum;                   // forward circular-mean sums M (same layout as Mbar)
+    int32_t* slot_arrivals;        // per (detector, radius block): units finished this call
+    int32_t* work_counters;        // dynamic work queues: [0..1] adjoint cells, [2..3] adjoint lists
     float* mbar;                   // adjoint Mbar
-    float* tv_partial;             // per image tile TV partial sums
+    float4* zbuf;                  // adjoint per-group cell sums
+    float* tv_partial;             // per image tile partial sums
     int32_t* status;               // device status word (bounded waits)
     int32_t n_inst;
-    int32_t n_fwd_ctas, n_fwd_tiles, n_adj_tiles, n_gather_tiles, n_img_tiles;
+    int32_t n_fwd_ctas, n_fwd_tiles, n_adj_tiles, n_cell_items, n_img_tiles, n_list_items;
     int32_t m_lanes, adj_groups;
-    int32_t smem_pitch_max;        // unused by kernels; for diagnostics
+    int32_t adj_mode;              // 1 = list mode, 0 = compute mode
+    int32_t cell_blocks;           // CTAs of the adjoint cell kernel (8 warps each)
     int32_t fwd_smem_bytes;        // dynamic shared memory of the circular-mean kernel
+    int32_t abel_smem_bytes;       // dynamic shared memory of the Abel kernels
     int32_t bf16;                  // image storage is BF16
-    int32_t tv_tiles_per_inst_max;
 };
+
+constexpr int kAbelJ = 4;          // detectors per Abel CTA
+constexpr int kAbelX = 32;         // outputs per Abel CTA (one per lane)
+constexpr int kAbelWarps = 8;      // warps per Abel CTA, splitting the contracted index
+constexpr int kAbelChunk = 2048;   // shared-memory chunk of the contracted index
 
 // Shared-memory row pitch (elements) of a band of an N-wide image.  The
 // pitch leaves a zero column on each side, keeps rows 16-byte aligned, and is

@@ -179,6 +179,7 @@ void mark_chunks(double U, double V, double rlo, double rhi, double x0, double x
 } // namespace
 
 static_assert(sizeof(InstDev) % 8 == 0, "InstDev layout");
+static_assert(sizeof(Unit) == 32, "Unit layout");
 
 pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const pat_options_t& opt,
                         cudaStream_t st)
@@ -190,7 +191,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const int ml = opt.m_lanes;
     const int qpiece = opt.q_piece;
     const int esize = bf16 ? 2 : 4;
-    const int G = 4;
+    const int G = 4; // angle chunk of the unit builder
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PAT_ERR_CUDA;
@@ -208,7 +209,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         P.g_offsets[i + 1] = P.g_offsets[i] + (int64_t)geoms[i].n_det * geoms[i].n_t;
     }
 
-    // ---- distinct K (trig) and n_t (Abel matrices) ------------------------
+    // ---- distinct K (trig) and n_t (Abel matrices P, then P^T) ------------
     std::map<int, int64_t> trig_off, p_off;
     std::vector<float2> trig;
     std::vector<float> pmat;
@@ -225,19 +226,24 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         const int nt = geoms[i].n_t;
         if (!p_off.count(nt)) {
             p_off[nt] = (int64_t)pmat.size();
+            const int nr = nt + 2;
             std::vector<float> Pm = build_abel_matrix(nt);
             pmat.insert(pmat.end(), Pm.begin(), Pm.end());
+            const size_t base = pmat.size();
+            pmat.resize(base + Pm.size());
+            for (int kk = 0; kk < nt; ++kk)
+                for (int m = 0; m < nr; ++m) pmat[base + (size_t)m * nt + kk] = Pm[(size_t)kk * nr + m];
         }
     }
 
     // ---- per-geometry templates (units, bands, slots) ---------------------
-    // Band rows: the shared band of a CTA holds at most `rows` image rows.
     std::map<GeomKey, int> tmpl_index;
     std::vector<GeomTemplate> tmpls;
     std::vector<int> inst_tmpl(n_inst);
     std::vector<float> detU, detV;
+    std::vector<float2> rtrig;
     std::vector<InstDev> inst(n_inst);
-    int smem_bytes = 0;
+    int band_bytes = 0;
     int bands_max = 0;
 
     for (int i = 0; i < n_inst; ++i) {
@@ -275,6 +281,24 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             detU.push_back((float)(std::cos(th) * (n / 2.0) - 0.5));
             detV.push_back((float)(std::sin(th) * (n / 2.0) - 0.5));
         }
+        // reciprocal ray slopes for the adjoint's slab test, from the FP32 table values
+        {
+            auto bits = [](int64_t v) { int b = 0; while ((1ll << b) < v) ++b; return std::max(b, 1); };
+            d.code_qbits = bits(g.n_angles);
+            d.code_mbits = bits(d.n_r);
+            P.code_bits_max = std::max(P.code_bits_max, d.code_qbits + d.code_mbits + bits(g.n_det));
+        }
+        d.rtrig_off = (int64_t)rtrig.size();
+        {
+            const float2* tq = &trig[d.trig_off];
+            auto rcp = [&](float c) {
+                const double x = (double)c * (double)d.delta;
+                if (std::fabs(x) < 1e-30) return 1e30f;
+                const double r = 1.0 / x;
+                return (float)std::max(-1e30, std::min(1e30, r));
+            };
+            for (int q = 0; q < 2 * g.n_angles; ++q) rtrig.push_back(make_float2(rcp(tq[q].x), rcp(tq[q].y)));
+        }
 
         GeomKey key{n, g.n_det, g.n_t, g.n_angles, bf16 ? 1 : 0, ml, qpiece, rows_max, g.arc_start, g.arc_span,
                     g.t_max};
@@ -294,7 +318,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             T.bands[b].lo = -1 + (int)(((int64_t)b * (n + 1)) / nb);
             T.bands[b].hi = -1 + (int)(((int64_t)(b + 1) * (n + 1)) / nb);
             const int rows = T.bands[b].hi - T.bands[b].lo + 1;
-            smem_bytes = std::max(smem_bytes, rows * W * esize);
+            band_bytes = std::max(band_bytes, rows * W * esize);
         }
         // Units: for every (band, detector, radius block) the angle chunks
         // whose sector can reach the band's cells, split into pieces.
@@ -314,8 +338,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                     mark_chunks(Uj[j], Vj[j], m0 * (double)d.delta - eps, m1 * (double)d.delta + eps, x0, x1, y0, y1,
                                 K, G, mark);
                     const int nch = (int)mark.size();
-                    // runs of marked chunks, with wrap-around
-                    std::vector<std::pair<int, int>> runs; // [c_begin, c_end) possibly c_end > nch for wrap
+                    std::vector<std::pair<int, int>> runs; // [c_begin, c_end), c_end > nch wraps
                     int c = 0;
                     while (c < nch) {
                         if (!mark[c]) { ++c; continue; }
@@ -353,9 +376,9 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (int b = 0; b < nb; ++b)
             for (int j = 0; j < g.n_det; ++j)
                 for (Unit& u : per[b][j]) {
-                    int32_t& c = T.slotcnt[(size_t)j * d.nmb + u.m0 / ml];
-                    u.slot = c++;
-                    T.n_slots = std::max(T.n_slots, (int)c);
+                    int32_t& cnt = T.slotcnt[(size_t)j * d.nmb + u.m0 / ml];
+                    u.slot = cnt++;
+                    T.n_slots = std::max(T.n_slots, (int)cnt);
                     T.slot_samples += (int64_t)u.nq * ml;
                 }
         for (int b = 0; b < nb; ++b) {
@@ -367,25 +390,30 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     }
 
     // ---- CTA schedule for the circular means ------------------------------
+    const int smem_bytes = band_bytes + kMaxSegUnits * (int)sizeof(Unit);
     if (smem_bytes > P.max_smem_optin) return PAT_ERR_UNSUPPORTED;
     P.fwd_smem = smem_bytes;
-    int bps = circmean_blocks_per_sm(ml, bf16, smem_bytes);
+    const int bps = circmean_blocks_per_sm(ml, bf16, smem_bytes);
     if (bps < 1) return PAT_ERR_UNSUPPORTED;
     const int n_ctas_target = bps * P.num_sms;
     double total_cost = 0.0;
     for (int i = 0; i < n_inst; ++i)
         for (auto& b : tmpls[inst_tmpl[i]].bands) total_cost += b.cost;
     const double seg_target = std::max(1.0, total_cost / (2.0 * n_ctas_target));
-    // split each template band into segments (units dealt round-robin by cost)
+    // split each template band into segments (units dealt by cost to the
+    // least-loaded segment, at most kMaxSegUnits units per segment)
     for (auto& T : tmpls)
         for (auto& band : T.bands) {
             std::vector<Unit>& us = band.units;
             std::stable_sort(us.begin(), us.end(), [](const Unit& a, const Unit& b) { return a.nq > b.nq; });
-            const int nseg = std::max(1, std::min((int)us.size(), (int)std::lround(band.cost / seg_target)));
+            int nseg = std::max(1, std::min((int)us.size(), (int)std::lround(band.cost / seg_target)));
+            nseg = std::max(nseg, (int)((us.size() + kMaxSegUnits - 1) / kMaxSegUnits));
             std::vector<std::vector<Unit>> bins(nseg);
             std::vector<double> cost(nseg, 0.0);
             for (const Unit& u : us) {
-                const int k = (int)(std::min_element(cost.begin(), cost.end()) - cost.begin());
+                int k = -1;
+                for (int s = 0; s < nseg; ++s)
+                    if ((int)bins[s].size() < kMaxSegUnits && (k < 0 || cost[s] < cost[k])) k = s;
                 bins[k].push_back(u);
                 cost[k] += u.nq + kUnitOverhead;
             }
@@ -397,7 +425,6 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                 us.insert(us.end(), bins[k].begin(), bins[k].end());
             }
         }
-    // global unit array
     std::vector<Unit> units;
     for (auto& T : tmpls) {
         T.band_unit_base.resize(T.bands.size());
@@ -406,7 +433,6 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             units.insert(units.end(), T.bands[b].units.begin(), T.bands[b].units.end());
         }
     }
-    // segments of every instance, LPT-assigned to CTAs
     struct SegC {
         Segment s;
         double cost;
@@ -447,10 +473,49 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     }
     if (segc.empty()) cta_seg.assign(1, 0);
 
+    // ---- adjoint cell items -------------------------------------------------
+    int64_t patches = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const int n = geoms[i].n;
+        patches += (int64_t)((n + 1 + kPatchW - 1) / kPatchW) * ((n + 1 + kPatchH - 1) / kPatchH);
+    }
+    const int cbps = adj_cells_blocks_per_sm();
+    if (cbps < 1) return PAT_ERR_UNSUPPORTED;
+    const int64_t resident_warps = (int64_t)cbps * P.num_sms * 8;
+    int AG = opt.adj_groups;
+    if (AG == 0) AG = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * resident_warps + patches - 1) / patches));
+    // Items with an estimate of their cost (candidate rays per detector, from
+    // the patch centre), sorted largest first for the kernel's dynamic queue.
+    std::vector<std::pair<double, CellItem>> wit;
+    for (int i = 0; i < n_inst; ++i) {
+        const InstDev& d = inst[i];
+        const int n = geoms[i].n;
+        const double R = 0.7111, per_rad = d.K / kTwoPi;
+        for (int y0 = -1; y0 <= n - 1; y0 += kPatchH)
+            for (int x0 = -1; x0 <= n - 1; x0 += kPatchW) {
+                const double px = x0 - d.c0 + 0.5 * kPatchW, py = y0 - d.c0 + 0.5 * kPatchH;
+                for (int gg = 0; gg < AG; ++gg) {
+                    double cost = 0.0;
+                    for (int j = gg; j < d.n_det; j += AG) {
+                        const double rc = std::hypot(px - detU[d.det_off + j], py - detV[d.det_off + j]);
+                        const double rays = rc <= 1.25 * R ? d.K : 2.0 * std::asin(std::min(1.0, R / rc)) * per_rad + 1;
+                        cost += 3.0 + rays;
+                    }
+                    wit.push_back({cost, CellItem{i, x0, y0, gg}});
+                }
+            }
+    }
+    std::stable_sort(wit.begin(), wit.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<CellItem> citems;
+    citems.reserve(wit.size());
+    for (auto& w : wit) citems.push_back(w.second);
+    const int cell_blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)cbps * P.num_sms, ((int64_t)citems.size() + 7) / 8));
+
     // ---- per-instance workspace offsets and slot counts -------------------
     std::vector<int32_t> slotcnt;
     std::map<int, int64_t> tmpl_slot_off;
-    int64_t mpart_total = 0, mbar_total = 0;
+    int64_t mpart_total = 0, mbar_total = 0, z_total = 0, arrive_total = 0;
     int64_t samples_slots = 0;
     for (int i = 0; i < n_inst; ++i) {
         const int ti = inst_tmpl[i];
@@ -466,22 +531,23 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         mpart_total += (int64_t)T.n_slots * d.n_det * d.n_r;
         d.mbar_off = mbar_total;
         mbar_total += (int64_t)d.n_det * d.n_r;
+        d.arrive_off = arrive_total;
+        arrive_total += (int64_t)d.n_det * d.nmb;
+        d.z_off = z_total;
+        z_total += (int64_t)AG * (d.n + 1) * (d.n + 1);
         samples_slots += T.slot_samples;
     }
 
-    // ---- tiles ------------------------------------------------------------
+    // ---- tiles --------------------------------------------------------------
     std::vector<TimeTile> fwd_tiles, adj_tiles;
-    std::vector<AdjTile> gtiles;
     std::vector<ImgTile> itiles;
     int64_t time_macs = 0;
     for (int i = 0; i < n_inst; ++i) {
         const InstDev& d = inst[i];
-        for (int j0 = 0; j0 < d.n_det; j0 += 16) {
-            for (int k0 = 0; k0 < d.n_t; k0 += 64) fwd_tiles.push_back({i, j0, k0, 0});
-            for (int m0 = 0; m0 < d.n_r; m0 += 64) adj_tiles.push_back({i, j0, m0, 0});
+        for (int j0 = 0; j0 < d.n_det; j0 += kAbelJ) {
+            for (int k0 = 0; k0 < d.n_t; k0 += kAbelX) fwd_tiles.push_back({i, j0, k0, 0});
+            for (int m0 = 0; m0 < d.n_r; m0 += kAbelX) adj_tiles.push_back({i, j0, m0, 0});
         }
-        for (int y0 = 0; y0 < d.n; y0 += kAdjOut)
-            for (int x0 = 0; x0 < d.n; x0 += kAdjOut) gtiles.push_back({i, x0, y0, 0});
         for (int y0 = 0; y0 < d.n; y0 += 8)
             for (int x0 = 0; x0 < d.n; x0 += 32) itiles.push_back({i, x0, y0, 0});
         // nonzeros of P: rows kk have m <= kk + 2 (kk = k - 1)
@@ -489,9 +555,9 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (int kk = 0; kk < d.n_t; ++kk) nnz += std::min(kk + 3, d.n_r);
         time_macs += nnz * d.n_det;
     }
-    // largest instances first for better tail behaviour
-    std::stable_sort(gtiles.begin(), gtiles.end(),
-                     [&](const AdjTile& a, const AdjTile& b) { return inst[a.inst].n_det > inst[b.inst].n_det; });
+    // larger Abel tiles first (the triangle makes late time tiles heavier)
+    std::stable_sort(fwd_tiles.begin(), fwd_tiles.end(), [](const TimeTile& a, const TimeTile& b) { return a.x0 > b.x0; });
+    std::stable_sort(adj_tiles.begin(), adj_tiles.end(), [](const TimeTile& a, const TimeTile& b) { return a.x0 < b.x0; });
 
     // ---- upload -----------------------------------------------------------
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -505,6 +571,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const size_t o_detU = reserve(sizeof(float) * detU.size());
     const size_t o_detV = reserve(sizeof(float) * detV.size());
     const size_t o_trig = reserve(sizeof(float2) * trig.size());
+    const size_t o_rtrig = reserve(sizeof(float2) * rtrig.size());
     const size_t o_P = reserve(sizeof(float) * pmat.size());
     const size_t o_slot = reserve(sizeof(int32_t) * slotcnt.size());
     const size_t o_units = reserve(sizeof(Unit) * units.size());
@@ -512,7 +579,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const size_t o_ctaseg = reserve(sizeof(int32_t) * cta_seg.size());
     const size_t o_ft = reserve(sizeof(TimeTile) * fwd_tiles.size());
     const size_t o_at = reserve(sizeof(TimeTile) * adj_tiles.size());
-    const size_t o_gt = reserve(sizeof(AdjTile) * gtiles.size());
+    const size_t o_ci = reserve(sizeof(CellItem) * citems.size());
     const size_t o_it = reserve(sizeof(ImgTile) * itiles.size());
     const size_t o_status = reserve(64);
     const size_t o_count = reserve(64);
@@ -530,6 +597,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     put(o_detU, detU.data(), sizeof(float) * detU.size());
     put(o_detV, detV.data(), sizeof(float) * detV.size());
     put(o_trig, trig.data(), sizeof(float2) * trig.size());
+    put(o_rtrig, rtrig.data(), sizeof(float2) * rtrig.size());
     put(o_P, pmat.data(), sizeof(float) * pmat.size());
     put(o_slot, slotcnt.data(), sizeof(int32_t) * slotcnt.size());
     put(o_units, units.data(), sizeof(Unit) * units.size());
@@ -537,18 +605,28 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     put(o_ctaseg, cta_seg.data(), sizeof(int32_t) * cta_seg.size());
     put(o_ft, fwd_tiles.data(), sizeof(TimeTile) * fwd_tiles.size());
     put(o_at, adj_tiles.data(), sizeof(TimeTile) * adj_tiles.size());
-    put(o_gt, gtiles.data(), sizeof(AdjTile) * gtiles.size());
+    put(o_ci, citems.data(), sizeof(CellItem) * citems.size());
     put(o_it, itiles.data(), sizeof(ImgTile) * itiles.size());
     if (cudaMemcpyAsync(P.d_tables, host.data(), P.tables_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return PAT_ERR_CUDA;
 
+    // workspace (floats): forward slots | Mbar | TV partials | (aligned) cell sums (float4)
+    // workspace (4-byte words): slots | M | Mbar | TV partials | arrival counters | cell sums (float4)
     const int64_t tv_parts = 2 * (int64_t)itiles.size();
-    P.work_floats = mpart_total + mbar_total + tv_parts;
+    const int64_t o_msum = mpart_total, o_mbar = o_msum + mbar_total, o_tvp = o_mbar + mbar_total;
+    const int64_t o_arr = o_tvp + tv_parts;
+    const int64_t o_ctr = o_arr + arrive_total;
+    const int64_t z_float_off = ((o_ctr + 16 + 63) / 64) * 64;
+    P.work_floats = z_float_off + 4 * z_total;
     if (cudaMalloc(&P.d_work, sizeof(float) * std::max<int64_t>(P.work_floats, 1)) != cudaSuccess) {
         P.d_work = nullptr;
         cudaGetLastError();
         return PAT_ERR_OOM;
     }
+    // zero everything once: circular-mean sums of blocks that no unit touches
+    // stay zero, and the arrival counters start (and are left by every call) at 0
+    if (cudaMemsetAsync(P.d_work, 0, sizeof(float) * std::max<int64_t>(P.work_floats, 1), st) != cudaSuccess)
+        return PAT_ERR_CUDA;
 
     unsigned char* base = static_cast<unsigned char*>(P.d_tables);
     DevPlan& dp = P.dp;
@@ -557,6 +635,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.detU = reinterpret_cast<const float*>(base + o_detU);
     dp.detV = reinterpret_cast<const float*>(base + o_detV);
     dp.trig = reinterpret_cast<const float2*>(base + o_trig);
+    dp.rtrig = reinterpret_cast<const float2*>(base + o_rtrig);
     dp.P = reinterpret_cast<const float*>(base + o_P);
     dp.slotcnt = reinterpret_cast<const uint8_t*>(base + o_slot);
     dp.units = reinterpret_cast<const Unit*>(base + o_units);
@@ -564,21 +643,29 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.cta_seg = reinterpret_cast<const int32_t*>(base + o_ctaseg);
     dp.fwd_tiles = reinterpret_cast<const TimeTile*>(base + o_ft);
     dp.adj_tiles = reinterpret_cast<const TimeTile*>(base + o_at);
-    dp.gather_tiles = reinterpret_cast<const AdjTile*>(base + o_gt);
+    dp.cell_items = reinterpret_cast<const CellItem*>(base + o_ci);
     dp.img_tiles = reinterpret_cast<const ImgTile*>(base + o_it);
     dp.mpart = P.d_work;
-    dp.mbar = P.d_work + mpart_total;
-    dp.tv_partial = P.d_work + mpart_total + mbar_total;
+    dp.msum = P.d_work + o_msum;
+    dp.mbar = P.d_work + o_mbar;
+    dp.tv_partial = P.d_work + o_tvp;
+    dp.slot_arrivals = reinterpret_cast<int32_t*>(P.d_work + o_arr);
+    dp.work_counters = reinterpret_cast<int32_t*>(P.d_work + o_ctr);
+    P.d_counters = reinterpret_cast<int32_t*>(P.d_work + o_arr);
+    P.counters_bytes = (size_t)(o_ctr + 16 - o_arr) * 4;
+    dp.zbuf = reinterpret_cast<float4*>(P.d_work + z_float_off);
     dp.status = reinterpret_cast<int32_t*>(base + o_status);
     dp.n_inst = n_inst;
     dp.n_fwd_ctas = (int)cta_seg.size() - 1;
     dp.n_fwd_tiles = (int)fwd_tiles.size();
     dp.n_adj_tiles = (int)adj_tiles.size();
-    dp.n_gather_tiles = (int)gtiles.size();
+    dp.n_cell_items = (int)citems.size();
     dp.n_img_tiles = (int)itiles.size();
     dp.m_lanes = ml;
-    dp.adj_groups = opt.adj_groups;
+    dp.adj_groups = AG;
+    dp.cell_blocks = cell_blocks;
     dp.fwd_smem_bytes = smem_bytes;
+    dp.abel_smem_bytes = kAbelChunk * (int)sizeof(float4);
     dp.bf16 = bf16 ? 1 : 0;
 
     // ---- sample count (exact, with the kernels' FP32 arithmetic) ----------
@@ -590,6 +677,95 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     if (cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return PAT_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
+
+    // ---- adjoint sample lists (list mode) --------------------------------------
+    const bool list_fits = P.code_bits_max <= 32;
+    bool use_lists = opt.adj_mode == 1 || (opt.adj_mode == 0 && list_fits &&
+                                           (double)count * 4.0 <= (double)P.list_budget_bytes);
+    if (opt.adj_mode == 1 && !list_fits) return PAT_ERR_UNSUPPORTED;
+    int64_t list_bytes = 0;
+    if (use_lists) {
+        // count the hits of every cell, per geometry template (first instance)
+        std::vector<int> rep(tmpls.size(), -1);
+        for (int i = 0; i < n_inst; ++i)
+            if (rep[inst_tmpl[i]] < 0) rep[inst_tmpl[i]] = i;
+        std::vector<std::vector<int32_t>> counts(tmpls.size());
+        int32_t* d_counts = nullptr;
+        int64_t max_cells = 0;
+        for (size_t t = 0; t < tmpls.size(); ++t)
+            max_cells = std::max<int64_t>(max_cells, (int64_t)(inst[rep[t]].n + 1) * (inst[rep[t]].n + 1));
+        if (cudaMalloc(&d_counts, sizeof(int32_t) * max_cells) != cudaSuccess) {
+            cudaGetLastError();
+            return PAT_ERR_OOM;
+        }
+        std::vector<int64_t> offs_all;
+        std::vector<int64_t> tmpl_list_off(tmpls.size());
+        int64_t codes_total = 0;
+        pat_status_t s = PAT_OK;
+        for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
+            const int i = rep[t];
+            const int cells = (inst[i].n + 1) * (inst[i].n + 1);
+            if (launch_adj_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, st) != cudaSuccess) s = PAT_ERR_CUDA;
+            counts[t].resize(cells);
+            if (s == PAT_OK && cudaMemcpyAsync(counts[t].data(), d_counts, sizeof(int32_t) * cells,
+                                               cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                s = PAT_ERR_CUDA;
+            if (s == PAT_OK && cudaStreamSynchronize(st) != cudaSuccess) s = PAT_ERR_CUDA;
+            tmpl_list_off[t] = (int64_t)offs_all.size();
+            for (int c = 0; c < cells; ++c) {
+                offs_all.push_back(codes_total);
+                codes_total += counts[t][c];
+            }
+            offs_all.push_back(codes_total);
+        }
+        cudaFree(d_counts);
+        if (s != PAT_OK) return s;
+        // cells of every instance, longest lists first
+        std::vector<std::pair<int32_t, int2>> li;
+        for (int i = 0; i < n_inst; ++i) {
+            const auto& cn = counts[inst_tmpl[i]];
+            for (int c = 0; c < (int)cn.size(); ++c) li.push_back({cn[c], make_int2(i, c)});
+        }
+        std::stable_sort(li.begin(), li.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+        const size_t b_offs = sizeof(int64_t) * offs_all.size();
+        const size_t b_items = sizeof(int2) * li.size();
+        const size_t b_codes = sizeof(uint32_t) * std::max<int64_t>(codes_total, 1);
+        const size_t o_items_l = align(b_offs), o_codes_l = align(o_items_l + b_items);
+        list_bytes = (int64_t)(o_codes_l + b_codes);
+        if (cudaMalloc(&P.d_lists, list_bytes) != cudaSuccess) {
+            P.d_lists = nullptr;
+            cudaGetLastError();
+            return PAT_ERR_OOM;
+        }
+        unsigned char* lb = static_cast<unsigned char*>(P.d_lists);
+        std::vector<int2> items(li.size());
+        for (size_t k = 0; k < li.size(); ++k) items[k] = li[k].second;
+        if (cudaMemcpyAsync(lb, offs_all.data(), b_offs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(lb + o_items_l, items.data(), b_items, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return PAT_ERR_CUDA;
+        dp.cell_off = reinterpret_cast<const int64_t*>(lb);
+        dp.list_items = reinterpret_cast<const int2*>(lb + o_items_l);
+        dp.codes = reinterpret_cast<const uint32_t*>(lb + o_codes_l);
+        for (int i = 0; i < n_inst; ++i) inst[i].list_off = tmpl_list_off[inst_tmpl[i]];
+        if (cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(InstDev) * inst.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+            return PAT_ERR_CUDA;
+        // fill the lists (same enumeration, same order)
+        for (size_t t = 0; t < tmpls.size(); ++t) {
+            const int i = rep[t];
+            if (launch_adj_build(dp, i, inst[i].n, nullptr, dp.cell_off + tmpl_list_off[t],
+                                 reinterpret_cast<uint32_t*>(lb + o_codes_l), st) != cudaSuccess)
+                return PAT_ERR_CUDA;
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
+        dp.n_list_items = (int)li.size();
+        dp.adj_mode = 1;
+        const int lbps = adj_list_blocks_per_sm();
+        if (lbps < 1) return PAT_ERR_UNSUPPORTED;
+        dp.cell_blocks = (int)std::max<int64_t>(
+            1, std::min<int64_t>((int64_t)lbps * P.num_sms, ((int64_t)li.size() + 7) / 8));
+        dp.adj_groups = 1;
+    }
 
     // ---- info -------------------------------------------------------------
     pat_plan_info_t& I = P.info;
@@ -608,7 +784,10 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     I.band_rows = 0;
     for (auto& T : tmpls)
         for (auto& b : T.bands) I.band_rows = std::max(I.band_rows, b.hi - b.lo + 1);
-    I.adj_groups = opt.adj_groups;
+    I.adj_groups = dp.adj_groups;
+    I.adj_mode = dp.adj_mode == 1 ? 1 : 2;
+    I.list_bytes = list_bytes;
+    I.device_bytes += list_bytes;
     I.bands_max = bands_max;
     return PAT_OK;
 }
@@ -625,6 +804,8 @@ void free_plan_memory(Plan& P)
     P.event_pool.clear();
     if (P.d_tables) cudaFree(P.d_tables);
     if (P.d_work) cudaFree(P.d_work);
+    if (P.d_lists) cudaFree(P.d_lists);
+    P.d_lists = nullptr;
     P.d_tables = nullptr;
     P.d_work = nullptr;
 }

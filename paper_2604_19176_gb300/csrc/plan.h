@@ -27,6 +27,11 @@ struct Plan {
     size_t tables_bytes = 0;
     float* d_work = nullptr;
     int64_t work_floats = 0;
+    int32_t* d_counters = nullptr;     // arrival counters + work queues (zero between calls)
+    size_t counters_bytes = 0;
+    void* d_lists = nullptr;           // adjoint sample lists (list mode)
+    int code_bits_max = 0;             // bits of a packed (j, m, q) sample code, largest instance
+    int64_t list_budget_bytes = 24ll << 30;
     int fwd_smem = 0;
     DevPlan dp{};
     pat_plan_info_t info{};
