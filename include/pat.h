@@ -226,6 +226,32 @@ typedef enum {
 pat_status_t pat_plan_set_timing(pat_plan_t plan, int32_t enable);
 pat_status_t pat_plan_kernel_times(pat_plan_t plan, double* total_ms, int64_t* launches, int32_t n_kinds);
 
+/*
+ * pat_tv_grad_noalloc — the TV value and gradient of pat_tv_grad for a batch
+ * of same-sized FP32 images, for callers that cannot allocate device memory.
+ * It needs no plan (creating a plan allocates) and allocates nothing.  The
+ * paper has no counterpart: this is a deployment variant of pat_tv_grad for
+ * code that runs under another framework's allocator, inside a real-time loop
+ * that must not call cudaMalloc after start-up, or anywhere allocation is not
+ * permitted.
+ *   d_f:     device FP32, batch images of n x n, row-major, packed (read only).
+ *   n:       image side, 1..16384.        batch: number of images, >= 1.
+ *   eps:     smoothing, > 0.
+ *   d_grad:  device FP32, same layout as d_f, overwritten with dTV/df (may be NULL).
+ *   d_value: device FP32, batch values (may be NULL; not both NULL).
+ *   Pointers 4-byte aligned, owned by the caller.
+ * Scratch: a fixed static device array of PAT_TV_NOALLOC_MAX_TILES floats
+ * (256 KB), one per 32 x 8 tile: batch * ceil(n/32) * ceil(n/8) must not
+ * exceed PAT_TV_NOALLOC_MAX_TILES, else PAT_ERR_INVALID_ARG and nothing is
+ * enqueued (e.g. n = 256 allows batch <= 256, n = 1024 allows batch <= 16).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make it before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU race; order them on one stream.
+ */
+#define PAT_TV_NOALLOC_MAX_TILES 65536
+pat_status_t pat_tv_grad_noalloc(const float* d_f, int32_t n, int32_t batch, float eps, float* d_grad,
+                                 float* d_value, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* pat_status_string(pat_status_t status);
 

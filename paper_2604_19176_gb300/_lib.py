@@ -22,7 +22,7 @@ STATUS_NAMES = {
 EXPORTED = (
     "pat_plan_create", "pat_plan_destroy", "pat_plan_layout", "pat_plan_info", "pat_forward",
     "pat_adjoint", "pat_tv_grad", "pat_residual", "pat_descent_step", "pat_plan_sync_status",
-    "pat_plan_set_timing", "pat_plan_kernel_times", "pat_status_string",
+    "pat_plan_set_timing", "pat_plan_kernel_times", "pat_tv_grad_noalloc", "pat_status_string",
 )
 KERNEL_KINDS = ("circmean", "abel_fwd", "abel_adj", "adjoint_gather", "tv", "residual", "descent")
 
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pat_plan_sync_status.argtypes = [vp, vp]
     lib.pat_plan_set_timing.argtypes = [vp, i32]
     lib.pat_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i64p, i32]
+    lib.pat_tv_grad_noalloc.argtypes = [vp, i32, i32, f32, vp, vp, vp]
     lib.pat_status_string.argtypes = [i32]
     lib.pat_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
