@@ -5,11 +5,13 @@
 // of f with zero outside the grid: the circular mean of the 2D Poisson
 // formula for the wave problem Eq. (1)-(2), discretised as in include/pat.h.
 //
-// Persistent CTAs.  CTA c owns segments cta_seg[c] .. cta_seg[c+1]-1.  For
-// each it stages the segment's image band (TMA bulk copies, one per image
-// row, completing on an mbarrier) and the segment's unit list in shared
-// memory; then its warps take units in order (largest first) from a shared
-// counter.  Lane l of a warp handles radius m0 + l % ML and angles
+// Persistent CTAs.  The work is split into band tasks (an image band of one
+// instance and the units whose samples can fall in it).  CTA c works on band
+// tasks cta_seg[c] .. cta_seg[c+1]-1; for each it stages the band in shared
+// memory (TMA bulk copies, one per image row, completing on an mbarrier) and
+// its warps take units, largest first, from the task's global queue, which
+// all CTAs assigned to the task share (the last one to finish re-arms it).
+// Lane l of a warp handles radius m0 + l % ML and angles
 // q0 + l / ML + i * (32 / ML); lanes walk along rays, so their 2 x 2 texel
 // reads are spatially coherent.  Each unit writes its own partial-sum slot,
 // so the result does not depend on scheduling.
@@ -51,9 +53,7 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_next;
-    Unit* su = reinterpret_cast<Unit*>(smem_raw);
-    T* s = reinterpret_cast<T*>(smem_raw + kMaxSegUnits * sizeof(Unit));
+    T* s = reinterpret_cast<T*>(smem_raw);
     constexpr int QL = kWarp / ML;
     constexpr int CO = ImgTraits<T>::col_off;
     const int lane = threadIdx.x & 31;
@@ -66,32 +66,27 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
     __syncthreads();
 
     uint32_t parity = 0;
-    const int seg_begin = dp.cta_seg[blockIdx.x], seg_end = dp.cta_seg[blockIdx.x + 1];
-    for (int sidx = seg_begin; sidx < seg_end; ++sidx) {
-        const Segment sg = dp.segs[sidx];
+    const int task_begin = dp.cta_seg[blockIdx.x], task_end = dp.cta_seg[blockIdx.x + 1];
+    for (int tidx = task_begin; tidx < task_end; ++tidx) {
+        const Segment sg = dp.segs[tidx];
         const InstDev in = dp.inst[sg.inst];
         const int n = in.n;
         const int W = ImgTraits<T>::pitch(n);
         const int rows = sg.band_hi - sg.band_lo + 1;
         const int nu = sg.unit_end - sg.unit_begin;
-        __syncthreads(); // every warp is done with the previous band and units
+        __syncthreads(); // every warp is done with the previous band
 
-        // ---- stage band rows and units (TMA bulk copies) -----------------
+        // ---- stage the band's image rows (TMA bulk copies) -----------------
         if (threadIdx.x < 32) {
             const int r0 = max(sg.band_lo, 0), r1 = min(sg.band_hi, n - 1);
             const uint32_t row_bytes = (uint32_t)n * sizeof(T);
             if (lane == 0) {
                 fence_proxy_async_smem();
-                const uint32_t total =
-                    (r1 >= r0 ? (uint32_t)(r1 - r0 + 1) * row_bytes : 0u) + (uint32_t)nu * (uint32_t)sizeof(Unit);
-                mbar_arrive_expect_tx(&bar, total);
-                s_next = 0;
+                mbar_arrive_expect_tx(&bar, r1 >= r0 ? (uint32_t)(r1 - r0 + 1) * row_bytes : 0u);
             }
             __syncwarp();
             for (int r = r0 + lane; r <= r1; r += 32)
                 bulk_g2s(s + (r - sg.band_lo) * W + CO, f + in.f_off + (size_t)r * n, row_bytes, &bar);
-            if (lane == 0 && nu > 0)
-                bulk_g2s(su, dp.units + sg.unit_begin, (uint32_t)nu * (uint32_t)sizeof(Unit), &bar);
         }
         // ---- zero borders: columns -1 and N.. (pad), rows outside the image
         const T zero = T(0.f);
@@ -112,7 +107,7 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
         }
         parity ^= 1u;
 
-        // ---- units --------------------------------------------------------
+        // ---- units: shared queue of every CTA working on this band task ----
         // cell (i0c, j0c) in centred units lives at s[j0c * W + i0c + base]
         const T* sb = s + ((in.c0 - sg.band_lo) * W + in.c0 + CO);
         const float ulo = (float)(-1 - in.c0), uhi = (float)(n - 1 - in.c0);
@@ -120,13 +115,22 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
         const float* detU = dp.detU + in.det_off;
         const float* detV = dp.detV + in.det_off;
         const float2* trig = dp.trig + in.trig_off;
+        const Unit* units = dp.units + sg.unit_begin;
+        int32_t* queue = dp.work_counters + kCircQueueBase + 2 * sg.queue;
 
-        for (;;) {
-            int u = 0;
-            if (lane == 0) u = atomicAdd(&s_next, 1);
-            u = __shfl_sync(0xffffffffu, u, 0);
-            if (u >= nu) break;
-            const Unit un = su[u];
+        int u = 0;
+        if (lane == 0) u = atomicAdd(queue, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        Unit un{};
+        if (u < nu) un = units[u];
+        while (u < nu) {
+            // take and fetch the next unit while this one is processed
+            int u2 = 0;
+            if (lane == 0) u2 = atomicAdd(queue, 1);
+            u2 = __shfl_sync(0xffffffffu, u2, 0);
+            Unit un2{};
+            if (u2 < nu) un2 = units[u2];
+
             const int m = un.m0 + ml;
             const float rho = (float)m * in.delta;
             const float U = __ldg(detU + un.j), V = __ldg(detV + un.j);
@@ -158,12 +162,20 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
             if (last) {
                 __threadfence();
                 if (ql == 0 && m < in.n_r) {
-                    float s = 0.f;
-                    for (int sl = 0; sl < total; ++sl) s += __ldcg(slots + (size_t)sl * plane + m);
-                    dp.msum[in.mbar_off + (size_t)un.j * in.n_r + m] = s;
+                    float sum = 0.f;
+                    for (int sl = 0; sl < total; ++sl) sum += __ldcg(slots + (size_t)sl * plane + m);
+                    dp.msum[in.mbar_off + (size_t)un.j * in.n_r + m] = sum;
                 }
                 if (lane == 0) dp.slot_arrivals[in.arrive_off + blk] = 0;
             }
+            u = u2;
+            un = un2;
+        }
+        // this CTA is done with the band task; its last participant re-arms the queue
+        __syncthreads();
+        if (threadIdx.x == 0 && atomicAdd(queue + 1, 1) == sg.parts - 1) {
+            queue[0] = 0;
+            queue[1] = 0;
         }
     }
 }

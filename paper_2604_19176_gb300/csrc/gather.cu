@@ -160,49 +160,74 @@ __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int
 }
 
 // ---------------------------------------------------------------------------
-// List mode: one warp per cell (queue sorted by list length); lanes stride the
-// cell's codes, recompute each sample exactly as the forward does, and the
-// four corner sums are reduced across the warp in a fixed tree.
+// List mode: thread = (cell, part of its list).  A warp owns an 8 x 4 patch
+// of cells and one of G contiguous parts of every cell's list (lists are
+// stored 16-byte aligned); each lane streams its part four codes at a time,
+// recomputes each sample exactly as the forward does and accumulates its
+// cell's corner sums in order.  Partial sums per part go to Z[part].
 // ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ void list_sample(const uint32_t code, int qb, int mbq, uint32_t mmask, uint32_t qmask,
+                                            const float2* __restrict__ det, const float2* __restrict__ trig,
+                                            const float* __restrict__ mb, int n_r, float delta, float cxf, float cyf,
+                                            float4& z)
+{
+    const int j = (int)(code >> mbq), m = (int)((code >> qb) & mmask), q = (int)(code & qmask);
+    const float2 cs = __ldg(trig + q);
+    const float2 UV = __ldg(det + j);
+    const float w = __ldg(mb + j * n_r + m);
+    const float rho = (float)m * delta;
+    const float u = __fmaf_rn(rho, cs.x, UV.x);
+    const float v = __fmaf_rn(rho, cs.y, UV.y);
+    // the sample lies in this cell, so floor(u) == cxf: a = u - floor(u)
+    add_corners(z, __fsub_rn(u, cxf), __fsub_rn(v, cyf), w);
+}
+} // namespace
+
 __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
 {
     const int lane = threadIdx.x & 31;
+    int32_t* ctr = dp.work_counters + 2;
+    const int G = dp.adj_groups;
     for (;;) {
-        const int item = take_item(dp.work_counters + 2, lane);
+        const int item = take_item(ctr, lane);
         if (item >= dp.n_list_items) break;
-        const int2 li = dp.list_items[item]; // (instance, cell index)
-        const InstDev in = dp.inst[li.x];
-        const int w = in.n + 1;
-        const float cxf = (float)(li.y % w - 1 - in.c0), cyf = (float)(li.y / w - 1 - in.c0);
-        const int64_t* off = dp.cell_off + in.list_off;
-        const int64_t beg = off[li.y], end = off[li.y + 1];
-        const float* detU = dp.detU + in.det_off;
-        const float* detV = dp.detV + in.det_off;
+        const CellItem it = dp.list_items[item];
+        const InstDev in = dp.inst[it.inst];
+        const int n = in.n, w = n + 1;
+        const int cx = it.x0 + (lane & (kPatchW - 1)), cy = it.y0 + lane / kPatchW;
+        if (cx > n - 1 || cy > n - 1) continue;
+        const int cell = (cy + 1) * w + (cx + 1);
+        const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
+        const int64_t beg = dp.cell_off[in.list_off + cell];       // multiple of 4
+        const int count = dp.cell_cnt[in.list_off + cell];
+        const int nv = (count + 3) >> 2;
+        const int v0 = (int)(((int64_t)it.group * nv) / G), v1 = (int)(((int64_t)(it.group + 1) * nv) / G);
+        const float2* det = reinterpret_cast<const float2*>(dp.detUV) + in.det_off;
         const float2* trig = dp.trig + in.trig_off;
         const float* mb = dp.mbar + in.mbar_off;
         const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
         const uint32_t qmask = (1u << qb) - 1u, mmask = (1u << in.code_mbits) - 1u;
+        const uint4* c4 = reinterpret_cast<const uint4*>(dp.codes + beg);
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t k = beg + lane; k < end; k += kWarp) {
-            const uint32_t code = __ldg(dp.codes + k);
-            const int j = (int)(code >> mbq), m = (int)((code >> qb) & mmask), q = (int)(code & qmask);
-            const float2 cs = __ldg(trig + q);
-            const float rho = (float)m * in.delta;
-            const float u = __fmaf_rn(rho, cs.x, __ldg(detU + j));
-            const float v = __fmaf_rn(rho, cs.y, __ldg(detV + j));
-            // the sample lies in this cell, so floor(u) == cxf: a = u - floor(u)
-            add_corners(z, __fsub_rn(u, cxf), __fsub_rn(v, cyf), __ldg(mb + (size_t)j * in.n_r + m));
-        }
+        // four 16-byte vectors in flight per lane, then their up to 16 samples
+        for (int vb = v0; vb < v1; vb += 4) {
+            uint4 c[4];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
-            z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
-            z.z += __shfl_xor_sync(0xffffffffu, z.z, o);
-            z.w += __shfl_xor_sync(0xffffffffu, z.w, o);
+            for (int u = 0; u < 4; ++u) c[u] = (vb + u < v1) ? __ldg(c4 + vb + u) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = (vb + u) * 4;
+                if (vb + u >= v1) break;
+                list_sample(c[u].x, qb, mbq, mmask, qmask, det, trig, mb, in.n_r, in.delta, cxf, cyf, z);
+                if (k + 1 < count) list_sample(c[u].y, qb, mbq, mmask, qmask, det, trig, mb, in.n_r, in.delta, cxf, cyf, z);
+                if (k + 2 < count) list_sample(c[u].z, qb, mbq, mmask, qmask, det, trig, mb, in.n_r, in.delta, cxf, cyf, z);
+                if (k + 3 < count) list_sample(c[u].w, qb, mbq, mmask, qmask, det, trig, mb, in.n_r, in.delta, cxf, cyf, z);
+            }
         }
-        if (lane == 0) dp.zbuf[in.z_off + li.y] = z;
+        dp.zbuf[in.z_off + (size_t)it.group * w * w + cell] = z;
     }
-    release_queue(dp.work_counters + 2, lane);
+    release_queue(ctr, lane);
 }
 
 template <typename T>
@@ -215,7 +240,7 @@ __global__ void __launch_bounds__(256) k_adj_combine(DevPlan dp, T* __restrict__
     if (px >= n || py >= n) return;
     const int w = n + 1;
     const float4* z = dp.zbuf + in.z_off;
-    const int groups = dp.adj_mode == 1 ? 1 : dp.adj_groups;
+    const int groups = dp.adj_groups;
     float s = 0.f;
     for (int g = 0; g < groups; ++g) {
         const float4* zg = z + (size_t)g * w * w;

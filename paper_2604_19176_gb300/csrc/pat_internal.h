@@ -29,7 +29,7 @@ constexpr int kColOff = 4;        // FP32 shared image: column 0 at word offset 
 constexpr int kColOffBF16 = 8;    // BF16 shared image: column 0 at element offset 8 (16 B aligned)
 constexpr int kPatchW = 8;        // adjoint: one warp owns an 8 x 4 patch of cells
 constexpr int kPatchH = 4;
-constexpr int kMaxSegUnits = 256; // circular-mean units staged per segment (shared memory)
+constexpr int kCircQueueBase = 4; // work_counters[4 + 2 t], [5 + 2 t]: queue of circular-mean band task t
 
 // Per-instance descriptor (device resident, read by every kernel).
 struct InstDev {
@@ -58,14 +58,17 @@ struct Unit {
     int32_t j, m0, q0, nq, slot, pad[3];
 };
 
-// A contiguous range of units of one (instance, band), processed by one CTA
-// after it has staged that band of the image in shared memory.
+// Band task of the circular means: the units [unit_begin, unit_end) of one
+// (instance, band), taken from a global queue by the `parts` CTAs that stage
+// this band of the image in shared memory.
 struct Segment {
     int32_t inst;
     int32_t band_lo;   // first cell row of the band (absolute, may be -1)
     int32_t band_hi;   // one past the last cell row (absolute, <= N)
     int32_t unit_begin, unit_end;
-    int32_t pad[3];
+    int32_t queue;     // index of the task's queue counters
+    int32_t parts;     // CTAs working on the task
+    int32_t pad;
 };
 
 // Output tile of the two Abel (time) stages: detectors [j0, j0 + kAbelJ),
@@ -101,13 +104,16 @@ struct DevPlan {
     const TimeTile* adj_tiles;
     const CellItem* cell_items;
     const ImgTile* img_tiles;
-    const int64_t* cell_off;       // adjoint list mode: per-cell ranges into codes
+    const float* detUV;            // (U_j, V_j) interleaved (float2), concatenated per instance
+    const int64_t* cell_off;       // adjoint list mode: start of each cell's codes (multiple of 4)
+    const int32_t* cell_cnt;       // adjoint list mode: number of codes of each cell
     const uint32_t* codes;         // adjoint list mode: packed (j, m, q) of every sample, by cell
-    const int2* list_items;        // adjoint list mode: (instance, cell), longest lists first
+    const CellItem* list_items;    // adjoint list mode: (patch, part) items, longest parts first
     float* mpart;                  // forward partial slots
     float* msum;                   // forward circular-mean sums M (same layout as Mbar)
     int32_t* slot_arrivals;        // per (detector, radius block): units finished this call
-    int32_t* work_counters;        // dynamic work queues: [0..1] adjoint cells, [2..3] adjoint lists
+    int32_t* work_counters;        // dynamic work queues: [0..1] adjoint cells, [2..3] adjoint lists,
+                                   // then two per circular-mean band task
     float* mbar;                   // adjoint Mbar
     float4* zbuf;                  // adjoint per-group cell sums
     float* tv_partial;             // per image tile partial sums

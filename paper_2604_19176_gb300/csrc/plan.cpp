@@ -390,41 +390,19 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     }
 
     // ---- CTA schedule for the circular means ------------------------------
-    const int smem_bytes = band_bytes + kMaxSegUnits * (int)sizeof(Unit);
+    // Band tasks: (instance, band) with the band's units, largest first.  Each
+    // task gets CTAs in proportion to its cost (at least one); the CTAs of a
+    // task share its unit queue.  Participants are placed on CTAs by LPT.
+    const int smem_bytes = band_bytes;
     if (smem_bytes > P.max_smem_optin) return PAT_ERR_UNSUPPORTED;
     P.fwd_smem = smem_bytes;
     const int bps = circmean_blocks_per_sm(ml, bf16, smem_bytes);
     if (bps < 1) return PAT_ERR_UNSUPPORTED;
     const int n_ctas_target = bps * P.num_sms;
-    double total_cost = 0.0;
-    for (int i = 0; i < n_inst; ++i)
-        for (auto& b : tmpls[inst_tmpl[i]].bands) total_cost += b.cost;
-    const double seg_target = std::max(1.0, total_cost / (2.0 * n_ctas_target));
-    // split each template band into segments (units dealt by cost to the
-    // least-loaded segment, at most kMaxSegUnits units per segment)
     for (auto& T : tmpls)
-        for (auto& band : T.bands) {
-            std::vector<Unit>& us = band.units;
-            std::stable_sort(us.begin(), us.end(), [](const Unit& a, const Unit& b) { return a.nq > b.nq; });
-            int nseg = std::max(1, std::min((int)us.size(), (int)std::lround(band.cost / seg_target)));
-            nseg = std::max(nseg, (int)((us.size() + kMaxSegUnits - 1) / kMaxSegUnits));
-            std::vector<std::vector<Unit>> bins(nseg);
-            std::vector<double> cost(nseg, 0.0);
-            for (const Unit& u : us) {
-                int k = -1;
-                for (int s = 0; s < nseg; ++s)
-                    if ((int)bins[s].size() < kMaxSegUnits && (k < 0 || cost[s] < cost[k])) k = s;
-                bins[k].push_back(u);
-                cost[k] += u.nq + kUnitOverhead;
-            }
-            us.clear();
-            for (int k = 0; k < nseg; ++k) {
-                if (bins[k].empty()) continue;
-                band.seg_ranges.emplace_back((int)us.size(), (int)(us.size() + bins[k].size()));
-                band.seg_cost.push_back(cost[k]);
-                us.insert(us.end(), bins[k].begin(), bins[k].end());
-            }
-        }
+        for (auto& band : T.bands)
+            std::stable_sort(band.units.begin(), band.units.end(),
+                             [](const Unit& a, const Unit& b) { return a.nq > b.nq; });
     std::vector<Unit> units;
     for (auto& T : tmpls) {
         T.band_unit_base.resize(T.bands.size());
@@ -433,36 +411,51 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             units.insert(units.end(), T.bands[b].units.begin(), T.bands[b].units.end());
         }
     }
-    struct SegC {
+    struct TaskC {
         Segment s;
         double cost;
     };
-    std::vector<SegC> segc;
+    std::vector<TaskC> tasks;
+    double total_cost = 0.0;
     for (int i = 0; i < n_inst; ++i) {
         const GeomTemplate& T = tmpls[inst_tmpl[i]];
-        for (size_t b = 0; b < T.bands.size(); ++b)
-            for (size_t k = 0; k < T.bands[b].seg_ranges.size(); ++k) {
-                Segment s{};
-                s.inst = i;
-                s.band_lo = T.bands[b].lo;
-                s.band_hi = T.bands[b].hi;
-                s.unit_begin = (int32_t)(T.band_unit_base[b] + T.bands[b].seg_ranges[k].first);
-                s.unit_end = (int32_t)(T.band_unit_base[b] + T.bands[b].seg_ranges[k].second);
-                segc.push_back({s, T.bands[b].seg_cost[k]});
-            }
+        for (size_t b = 0; b < T.bands.size(); ++b) {
+            if (T.bands[b].units.empty()) continue;
+            Segment s{};
+            s.inst = i;
+            s.band_lo = T.bands[b].lo;
+            s.band_hi = T.bands[b].hi;
+            s.unit_begin = (int32_t)T.band_unit_base[b];
+            s.unit_end = (int32_t)(T.band_unit_base[b] + T.bands[b].units.size());
+            s.queue = (int32_t)tasks.size();
+            tasks.push_back({s, T.bands[b].cost});
+            total_cost += T.bands[b].cost;
+        }
     }
-    std::stable_sort(segc.begin(), segc.end(), [](const SegC& a, const SegC& b) { return a.cost > b.cost; });
-    const int n_ctas = std::max(1, std::min(n_ctas_target, (int)segc.size()));
+    struct PartC {
+        int task;
+        double cost;
+    };
+    std::vector<PartC> parts;
+    for (size_t t = 0; t < tasks.size(); ++t) {
+        const double share = tasks[t].cost / std::max(total_cost, 1.0) * n_ctas_target;
+        const int nunits = tasks[t].s.unit_end - tasks[t].s.unit_begin;
+        const int np = std::max(1, std::min((int)std::lround(share), std::max(1, nunits / 2)));
+        tasks[t].s.parts = np;
+        for (int k = 0; k < np; ++k) parts.push_back({(int)t, tasks[t].cost / np});
+    }
+    std::stable_sort(parts.begin(), parts.end(), [](const PartC& a, const PartC& b) { return a.cost > b.cost; });
+    const int n_ctas = std::max(1, std::min(n_ctas_target, (int)parts.size()));
     std::vector<std::vector<Segment>> cta_lists(n_ctas);
     {
         using E = std::pair<double, int>;
         std::priority_queue<E, std::vector<E>, std::greater<E>> pq;
         for (int c = 0; c < n_ctas; ++c) pq.push({0.0, c});
-        for (const SegC& s : segc) {
+        for (const PartC& p : parts) {
             E e = pq.top();
             pq.pop();
-            cta_lists[e.second].push_back(s.s);
-            pq.push({e.first + s.cost + 4.0 * kUnitOverhead, e.second});
+            cta_lists[e.second].push_back(tasks[p.task].s);
+            pq.push({e.first + p.cost + 8.0 * kUnitOverhead, e.second});
         }
     }
     std::vector<Segment> segs;
@@ -471,7 +464,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         segs.insert(segs.end(), l.begin(), l.end());
         cta_seg.push_back((int32_t)segs.size());
     }
-    if (segc.empty()) cta_seg.assign(1, 0);
+    if (parts.empty()) cta_seg.assign(1, 0);
+    const int64_t n_band_tasks = (int64_t)tasks.size();
 
     // ---- adjoint cell items -------------------------------------------------
     int64_t patches = 0;
@@ -482,6 +476,14 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const int cbps = adj_cells_blocks_per_sm();
     if (cbps < 1) return PAT_ERR_UNSUPPORTED;
     const int64_t resident_warps = (int64_t)cbps * P.num_sms * 8;
+    // adjoint list mode is chosen here (the sample count used for the budget is
+    // the forward's evaluated-sample upper bound); its groups split each list
+    int64_t slot_samples_all = 0;
+    for (int i = 0; i < n_inst; ++i) slot_samples_all += tmpls[inst_tmpl[i]].slot_samples;
+    const bool list_fits = P.code_bits_max <= 32;
+    if (opt.adj_mode == 1 && !list_fits) return PAT_ERR_UNSUPPORTED;
+    const bool use_lists = opt.adj_mode == 1 || (opt.adj_mode == 0 && list_fits &&
+                                                 (double)slot_samples_all * 4.0 <= (double)P.list_budget_bytes);
     int AG = opt.adj_groups;
     if (AG == 0) AG = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * resident_warps + patches - 1) / patches));
     // Items with an estimate of their cost (candidate rays per detector, from
@@ -506,6 +508,15 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             }
     }
     std::stable_sort(wit.begin(), wit.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    int LG = 1;
+    if (use_lists) {
+        const int lbps = adj_list_blocks_per_sm();
+        if (lbps < 1) return PAT_ERR_UNSUPPORTED;
+        const int64_t lres = (int64_t)lbps * P.num_sms * 8;
+        LG = opt.adj_groups > 0 ? opt.adj_groups
+                                : (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * lres + patches - 1) / patches));
+    }
+    const int ZG = use_lists ? LG : AG;
     std::vector<CellItem> citems;
     citems.reserve(wit.size());
     for (auto& w : wit) citems.push_back(w.second);
@@ -534,7 +545,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         d.arrive_off = arrive_total;
         arrive_total += (int64_t)d.n_det * d.nmb;
         d.z_off = z_total;
-        z_total += (int64_t)AG * (d.n + 1) * (d.n + 1);
+        z_total += (int64_t)ZG * (d.n + 1) * (d.n + 1);
         samples_slots += T.slot_samples;
     }
 
@@ -570,6 +581,9 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const size_t o_inst = reserve(sizeof(InstDev) * inst.size());
     const size_t o_detU = reserve(sizeof(float) * detU.size());
     const size_t o_detV = reserve(sizeof(float) * detV.size());
+    std::vector<float2> detUV(detU.size());
+    for (size_t k = 0; k < detU.size(); ++k) detUV[k] = make_float2(detU[k], detV[k]);
+    const size_t o_detUV = reserve(sizeof(float2) * detUV.size());
     const size_t o_trig = reserve(sizeof(float2) * trig.size());
     const size_t o_rtrig = reserve(sizeof(float2) * rtrig.size());
     const size_t o_P = reserve(sizeof(float) * pmat.size());
@@ -596,6 +610,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     put(o_inst, inst.data(), sizeof(InstDev) * inst.size());
     put(o_detU, detU.data(), sizeof(float) * detU.size());
     put(o_detV, detV.data(), sizeof(float) * detV.size());
+    put(o_detUV, detUV.data(), sizeof(float2) * detUV.size());
     put(o_trig, trig.data(), sizeof(float2) * trig.size());
     put(o_rtrig, rtrig.data(), sizeof(float2) * rtrig.size());
     put(o_P, pmat.data(), sizeof(float) * pmat.size());
@@ -616,7 +631,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const int64_t o_msum = mpart_total, o_mbar = o_msum + mbar_total, o_tvp = o_mbar + mbar_total;
     const int64_t o_arr = o_tvp + tv_parts;
     const int64_t o_ctr = o_arr + arrive_total;
-    const int64_t z_float_off = ((o_ctr + 16 + 63) / 64) * 64;
+    const int64_t n_ctr = kCircQueueBase + 2 * n_band_tasks;
+    const int64_t z_float_off = ((o_ctr + n_ctr + 63) / 64) * 64;
     P.work_floats = z_float_off + 4 * z_total;
     if (cudaMalloc(&P.d_work, sizeof(float) * std::max<int64_t>(P.work_floats, 1)) != cudaSuccess) {
         P.d_work = nullptr;
@@ -634,6 +650,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.inst = reinterpret_cast<const InstDev*>(base + o_inst);
     dp.detU = reinterpret_cast<const float*>(base + o_detU);
     dp.detV = reinterpret_cast<const float*>(base + o_detV);
+    dp.detUV = reinterpret_cast<const float*>(base + o_detUV);
     dp.trig = reinterpret_cast<const float2*>(base + o_trig);
     dp.rtrig = reinterpret_cast<const float2*>(base + o_rtrig);
     dp.P = reinterpret_cast<const float*>(base + o_P);
@@ -652,7 +669,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.slot_arrivals = reinterpret_cast<int32_t*>(P.d_work + o_arr);
     dp.work_counters = reinterpret_cast<int32_t*>(P.d_work + o_ctr);
     P.d_counters = reinterpret_cast<int32_t*>(P.d_work + o_arr);
-    P.counters_bytes = (size_t)(o_ctr + 16 - o_arr) * 4;
+    P.counters_bytes = (size_t)(o_ctr + n_ctr - o_arr) * 4;
     dp.zbuf = reinterpret_cast<float4*>(P.d_work + z_float_off);
     dp.status = reinterpret_cast<int32_t*>(base + o_status);
     dp.n_inst = n_inst;
@@ -679,10 +696,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
 
     // ---- adjoint sample lists (list mode) --------------------------------------
-    const bool list_fits = P.code_bits_max <= 32;
-    bool use_lists = opt.adj_mode == 1 || (opt.adj_mode == 0 && list_fits &&
-                                           (double)count * 4.0 <= (double)P.list_budget_bytes);
-    if (opt.adj_mode == 1 && !list_fits) return PAT_ERR_UNSUPPORTED;
+    // Each cell's codes are stored 16-byte aligned (offsets are multiples of 4).
     int64_t list_bytes = 0;
     if (use_lists) {
         // count the hits of every cell, per geometry template (first instance)
@@ -699,6 +713,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             return PAT_ERR_OOM;
         }
         std::vector<int64_t> offs_all;
+        std::vector<int32_t> cnt_all;
         std::vector<int64_t> tmpl_list_off(tmpls.size());
         int64_t codes_total = 0;
         pat_status_t s = PAT_OK;
@@ -714,23 +729,35 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             tmpl_list_off[t] = (int64_t)offs_all.size();
             for (int c = 0; c < cells; ++c) {
                 offs_all.push_back(codes_total);
-                codes_total += counts[t][c];
+                cnt_all.push_back(counts[t][c]);
+                codes_total += (counts[t][c] + 3) & ~3;
             }
-            offs_all.push_back(codes_total);
         }
         cudaFree(d_counts);
         if (s != PAT_OK) return s;
-        // cells of every instance, longest lists first
-        std::vector<std::pair<int32_t, int2>> li;
+        if (codes_total >= ((int64_t)1 << 40)) return PAT_ERR_UNSUPPORTED;
+        // list-mode work items: (patch, part), by the longest part in the patch
+        std::vector<std::pair<int32_t, CellItem>> li;
         for (int i = 0; i < n_inst; ++i) {
             const auto& cn = counts[inst_tmpl[i]];
-            for (int c = 0; c < (int)cn.size(); ++c) li.push_back({cn[c], make_int2(i, c)});
+            const int n = inst[i].n, w = n + 1;
+            for (int y0 = -1; y0 <= n - 1; y0 += kPatchH)
+                for (int x0 = -1; x0 <= n - 1; x0 += kPatchW) {
+                    int32_t mx = 0;
+                    for (int dy = 0; dy < kPatchH; ++dy)
+                        for (int dx = 0; dx < kPatchW; ++dx) {
+                            const int cx = x0 + dx, cy = y0 + dy;
+                            if (cx <= n - 1 && cy <= n - 1) mx = std::max(mx, cn[(size_t)(cy + 1) * w + cx + 1]);
+                        }
+                    for (int gg = 0; gg < LG; ++gg) li.push_back({mx, CellItem{i, x0, y0, gg}});
+                }
         }
         std::stable_sort(li.begin(), li.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
         const size_t b_offs = sizeof(int64_t) * offs_all.size();
-        const size_t b_items = sizeof(int2) * li.size();
-        const size_t b_codes = sizeof(uint32_t) * std::max<int64_t>(codes_total, 1);
-        const size_t o_items_l = align(b_offs), o_codes_l = align(o_items_l + b_items);
+        const size_t b_cnt = sizeof(int32_t) * cnt_all.size();
+        const size_t b_items = sizeof(CellItem) * li.size();
+        const size_t b_codes = sizeof(uint32_t) * std::max<int64_t>(codes_total, 4);
+        const size_t o_cnt_l = align(b_offs), o_items_l = align(o_cnt_l + b_cnt), o_codes_l = align(o_items_l + b_items);
         list_bytes = (int64_t)(o_codes_l + b_codes);
         if (cudaMalloc(&P.d_lists, list_bytes) != cudaSuccess) {
             P.d_lists = nullptr;
@@ -738,13 +765,16 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             return PAT_ERR_OOM;
         }
         unsigned char* lb = static_cast<unsigned char*>(P.d_lists);
-        std::vector<int2> items(li.size());
+        std::vector<CellItem> items(li.size());
         for (size_t k = 0; k < li.size(); ++k) items[k] = li[k].second;
         if (cudaMemcpyAsync(lb, offs_all.data(), b_offs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(lb + o_items_l, items.data(), b_items, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            cudaMemcpyAsync(lb + o_cnt_l, cnt_all.data(), b_cnt, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(lb + o_items_l, items.data(), b_items, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemsetAsync(lb + o_codes_l, 0, b_codes, st) != cudaSuccess)
             return PAT_ERR_CUDA;
         dp.cell_off = reinterpret_cast<const int64_t*>(lb);
-        dp.list_items = reinterpret_cast<const int2*>(lb + o_items_l);
+        dp.cell_cnt = reinterpret_cast<const int32_t*>(lb + o_cnt_l);
+        dp.list_items = reinterpret_cast<const CellItem*>(lb + o_items_l);
         dp.codes = reinterpret_cast<const uint32_t*>(lb + o_codes_l);
         for (int i = 0; i < n_inst; ++i) inst[i].list_off = tmpl_list_off[inst_tmpl[i]];
         if (cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(InstDev) * inst.size(), cudaMemcpyHostToDevice, st) !=
@@ -761,10 +791,9 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         dp.n_list_items = (int)li.size();
         dp.adj_mode = 1;
         const int lbps = adj_list_blocks_per_sm();
-        if (lbps < 1) return PAT_ERR_UNSUPPORTED;
         dp.cell_blocks = (int)std::max<int64_t>(
             1, std::min<int64_t>((int64_t)lbps * P.num_sms, ((int64_t)li.size() + 7) / 8));
-        dp.adj_groups = 1;
+        dp.adj_groups = LG;
     }
 
     // ---- info -------------------------------------------------------------
