@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
                 if (ql == 0 && m < in.n_r) {
                     float sum = 0.f;
                     for (int sl = 0; sl < total; ++sl) sum += __ldcg(slots + (size_t)sl * plane + m);
-                    dp.msum[in.mbar_off + (size_t)un.j * in.n_r + m] = sum;
+                    dp.msum[in.mbar_off + (size_t)un.j * in.n_rp + m] = sum;
                 }
                 if (lane == 0) dp.slot_arrivals[in.arrive_off + blk] = 0;
             }

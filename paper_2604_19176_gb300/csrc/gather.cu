@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256, 5) k_adj_cells(DevPlan dp)
         const float* mb = dp.mbar + in.mbar_off;
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         enumerate_cell(dp, in, cxf, cyf, it.group, G, [&](int j, int m, int, float u, float v) {
-            add_corners(z, __fsub_rn(u, cxf), __fsub_rn(v, cyf), __ldg(mb + (size_t)j * in.n_r + m));
+            add_corners(z, __fsub_rn(u, cxf), __fsub_rn(v, cyf), __ldg(mb + (size_t)j * in.n_rp + m));
         });
         dp.zbuf[in.z_off + (size_t)it.group * (n + 1) * (n + 1) + (size_t)(cy + 1) * (n + 1) + (cx + 1)] = z;
     }
@@ -169,13 +169,13 @@ __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int
 namespace {
 __device__ __forceinline__ void list_sample(const uint32_t code, int qb, int mbq, uint32_t mmask, uint32_t qmask,
                                             const float2* __restrict__ det, const float2* __restrict__ trig,
-                                            const float* __restrict__ mb, int n_r, float delta, float cxf, float cyf,
+                                            const float* __restrict__ mb, int n_rp, float delta, float cxf, float cyf,
                                             float4& z)
 {
     const int j = (int)(code >> mbq), m = (int)((code >> qb) & mmask), q = (int)(code & qmask);
     const float2 cs = __ldg(trig + q);
     const float2 UV = __ldg(det + j);
-    const float w = __ldg(mb + j * n_r + m);
+    const float w = __ldg(mb + j * n_rp + m);
     const float rho = (float)m * delta;
     const float u = __fmaf_rn(rho, cs.x, UV.x);
     const float v = __fmaf_rn(rho, cs.y, UV.y);
@@ -219,10 +219,10 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
             for (int u = 0; u < 4; ++u) {
                 const int k = (vb + u) * 4;
                 if (vb + u >= v1) break;
-                list_sample(c[u].x, qb, mbq, mmask, qmask, det, trig, mb, in.n_r, in.delta, cxf, cyf, z);
-                if (k + 1 < count) list_sample(c[u].y, qb, mbq, mmask, qmask, det, trig, mb, in.n_r, in.delta, cxf, cyf, z);
-                if (k + 2 < count) list_sample(c[u].z, qb, mbq, mmask, qmask, det, trig, mb, in.n_r, in.delta, cxf, cyf, z);
-                if (k + 3 < count) list_sample(c[u].w, qb, mbq, mmask, qmask, det, trig, mb, in.n_r, in.delta, cxf, cyf, z);
+                list_sample(c[u].x, qb, mbq, mmask, qmask, det, trig, mb, in.n_rp, in.delta, cxf, cyf, z);
+                if (k + 1 < count) list_sample(c[u].y, qb, mbq, mmask, qmask, det, trig, mb, in.n_rp, in.delta, cxf, cyf, z);
+                if (k + 2 < count) list_sample(c[u].z, qb, mbq, mmask, qmask, det, trig, mb, in.n_rp, in.delta, cxf, cyf, z);
+                if (k + 3 < count) list_sample(c[u].w, qb, mbq, mmask, qmask, det, trig, mb, in.n_rp, in.delta, cxf, cyf, z);
             }
         }
         dp.zbuf[in.z_off + (size_t)it.group * w * w + cell] = z;

@@ -40,14 +40,16 @@ struct InstDev {
     int32_t n_slots, nmb;          // forward partial slots; radius blocks per detector
     int64_t f_off, g_off;          // element offsets of the instance's image / data
     int64_t mpart_off;             // float offset of forward partial slots (n_slots x n_det x n_r)
-    int64_t mbar_off;              // float offset of the adjoint's Mbar (n_det x n_r)
-    int64_t p_off;                 // float offset of the Abel matrix P (n_t x n_r) and of P^T (n_r x n_t)
+    int64_t mbar_off;              // float offset of M and of Mbar (n_det rows of pitch n_rp)
+    int64_t p_off;                 // float offset of P (n_t rows, pitch n_rp), then P^T (n_r rows, pitch n_tp)
     int64_t slotcnt_off;           // byte offset of the slot counts (n_det x nmb int32)
     int64_t z_off;                 // float4 offset of the adjoint cell sums (groups x (n+1)^2)
     int64_t rtrig_off;             // float2 offset of (1/(cos_q delta), 1/(sin_q delta)), 2K entries
     int64_t arrive_off;            // int offset of the slot-arrival counters (n_det x nmb)
     int64_t list_off;              // adjoint list mode: offset of the (n+1)^2 + 1 cell offsets
     int32_t code_qbits, code_mbits; // adjoint list mode: code = j << (qb+mb) | m << qb | q
+    int32_t n_rp;                  // row pitch (multiple of 32) of M, Mbar and P
+    int32_t n_tp;                  // row pitch (multiple of 32) of P^T
 };
 
 // Circular-mean work unit: radii [m0, m0 + m_lanes) of detector j, angles
@@ -131,7 +133,7 @@ struct DevPlan {
 constexpr int kAbelJ = 4;          // detectors per Abel CTA
 constexpr int kAbelX = 32;         // outputs per Abel CTA (one per lane)
 constexpr int kAbelWarps = 8;      // warps per Abel CTA, splitting the contracted index
-constexpr int kAbelChunk = 2048;   // shared-memory chunk of the contracted index
+constexpr int kAbelChunk = 512;    // rows of the P slice staged in shared memory at a time
 
 // Shared-memory row pitch (elements) of a band of an N-wide image.  The
 // pitch leaves a zero column on each side, keeps rows 16-byte aligned, and is

@@ -225,14 +225,17 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         }
         const int nt = geoms[i].n_t;
         if (!p_off.count(nt)) {
+            // P (nt rows, pitch nrp) then P^T (nr rows, pitch ntp); padding is zero
             p_off[nt] = (int64_t)pmat.size();
-            const int nr = nt + 2;
+            const int nr = nt + 2, nrp = (nr + 31) & ~31, ntp = (nt + 31) & ~31;
             std::vector<float> Pm = build_abel_matrix(nt);
-            pmat.insert(pmat.end(), Pm.begin(), Pm.end());
             const size_t base = pmat.size();
-            pmat.resize(base + Pm.size());
+            pmat.resize(base + (size_t)nt * nrp + (size_t)nr * ntp, 0.0f);
             for (int kk = 0; kk < nt; ++kk)
-                for (int m = 0; m < nr; ++m) pmat[base + (size_t)m * nt + kk] = Pm[(size_t)kk * nr + m];
+                for (int m = 0; m < nr; ++m) {
+                    pmat[base + (size_t)kk * nrp + m] = Pm[(size_t)kk * nr + m];
+                    pmat[base + (size_t)nt * nrp + (size_t)m * ntp + kk] = Pm[(size_t)kk * nr + m];
+                }
         }
     }
 
@@ -262,6 +265,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         d.n_det = g.n_det;
         d.n_t = g.n_t;
         d.n_r = g.n_t + 2;
+        d.n_rp = (d.n_r + 31) & ~31;
+        d.n_tp = (g.n_t + 31) & ~31;
         d.K = g.n_angles;
         d.c0 = n / 2;
         const double delta = g.t_max * n / (2.0 * g.n_t); // r_m / h = m * delta
@@ -541,7 +546,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         d.mpart_off = mpart_total;
         mpart_total += (int64_t)T.n_slots * d.n_det * d.n_r;
         d.mbar_off = mbar_total;
-        mbar_total += (int64_t)d.n_det * d.n_r;
+        mbar_total += (int64_t)d.n_det * d.n_rp;
         d.arrive_off = arrive_total;
         arrive_total += (int64_t)d.n_det * d.nmb;
         d.z_off = z_total;
@@ -682,7 +687,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.adj_groups = AG;
     dp.cell_blocks = cell_blocks;
     dp.fwd_smem_bytes = smem_bytes;
-    dp.abel_smem_bytes = kAbelChunk * (int)sizeof(float4);
+    dp.abel_smem_bytes = kAbelChunk * kWarp * (int)sizeof(float) + kAbelChunk * (int)sizeof(float4);
     dp.bf16 = bf16 ? 1 : 0;
 
     // ---- sample count (exact, with the kernels' FP32 arithmetic) ----------
