@@ -47,7 +47,7 @@ BYTES_PER_SAMPLE = 16              # 4 FP32 texels per bilinear sample
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -79,7 +79,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -126,9 +126,12 @@ def load_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the CUDA sources, to invalidate stored ncu traffic after a change."""
     h = hashlib.sha256()
-    for f in ("kernels.cu", "pat_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2604_19176_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2604_19176_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -252,21 +255,20 @@ def main():
         x /= nrm
     tau = 1.0 / (nrm + 8.0 * LAM / EPS)
 
-    f = torch.zeros_like(f_t)
+    f_bufs = [torch.zeros_like(f_t), torch.zeros_like(f_t)]
     g_pred = torch.empty_like(g_meas)
-    r = torch.empty_like(g_meas)
-    f_adj = torch.empty_like(f)
-    tvg = torch.empty_like(f)
+    f_adj = torch.empty_like(f_t)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    it = [0]
 
     def step():
-        plan.forward(f, out=g_pred)
-        plan.residual(g_pred, g_meas, out=r)
-        plan.adjoint(r, out=f_adj)
-        plan.tv_grad(f, EPS, grad=tvg, want_value=False)
-        plan.descent_step(f, f_adj, tvg, tau, LAM, nonneg=True)
+        # one fused projected-gradient TV iteration (pat_tv_step): A f, residual,
+        # A^T r, TV gradient and update, ping-ponging the image buffers
+        k = it[0]
+        plan.tv_step(f_bufs[k & 1], f_bufs[(k + 1) & 1], g_meas, tau, LAM, EPS, nonneg=True)
+        it[0] = k + 1
 
-    launches_per_step = 2 + 1 + 2 + 1 + 1
+    launches_per_step = 5  # circular means, Abel forward+residual, Abel adjoint, adjoint gather, TV update
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -331,12 +333,12 @@ def main():
     # ---- end to end through the public API with host buffers ------------
     e2e = None
     if not args.profile:
-        h_f = torch.empty(f.shape, dtype=torch.float32, pin_memory=True)
+        h_f = torch.empty(f_t.shape, dtype=torch.float32, pin_memory=True)
         h_f.copy_(f_t.cpu())
         h_g = torch.empty(g_meas.shape, dtype=torch.float32, pin_memory=True)
         h_g.copy_(g_meas.cpu())
-        h_out = torch.empty(f.shape, dtype=torch.float32, pin_memory=True)
-        d_f = torch.empty_like(f)
+        h_out = torch.empty(f_t.shape, dtype=torch.float32, pin_memory=True)
+        d_f = torch.empty_like(f_t)
         d_g = torch.empty_like(g_meas)
         e_ms = []
         for i in range(min(n_steps, 100) + 3):
@@ -369,7 +371,7 @@ def main():
                 "config": {"workload": WORKLOAD, "N": g.n, "n_det": g.n_det, "arc_deg": 180, "n_t": g.n_t,
                            "K": g.n_angles, "lambda": LAM, "tv_eps": EPS, "noise": "1% of max|g|",
                            "l2": "flushed (256 MB write) before every timed step, outside the events",
-                           "step": "A f, residual, A^T r, TV gradient, projected update"},
+                           "step": "pat_tv_step: A f, residual, A^T r, TV gradient, projected update"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * n_steps,
                 "samples_per_application": samples, "sample_slots": info["sample_slots"],

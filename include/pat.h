@@ -204,6 +204,22 @@ pat_status_t pat_descent_step(pat_plan_t plan, float* d_f, const float* d_adj,
                               float* d_delta, void* stream);
 
 /*
+ * pat_tv_step — one projected-gradient iteration of the TV reconstruction of
+ * Eq. (4), min_{f >= 0} 1/2 ||A f - g||^2 + lam TV_eps(f):
+ *     r = A f_in - g;   f_out = max(0, f_in - tau (A^T r + lam grad TV_eps(f_in)))
+ * (the max only when nonneg != 0).  Same result as pat_forward, pat_residual,
+ * pat_adjoint, pat_tv_grad and pat_descent_step in sequence, in fewer kernels:
+ * the residual is formed in the time stage of A, and the adjoint's final pixel
+ * sums, the TV gradient and the update share one kernel.  FP32 plans.
+ *   d_f_in:  device FP32 images (read only).   d_f_out: device FP32 images,
+ *            overwritten; must not alias d_f_in (the TV stencil reads the old
+ *            neighbours).   d_g: device FP32 measured data (read only).
+ *   d_delta: nullable, two values per instance as in pat_descent_step.
+ */
+pat_status_t pat_tv_step(pat_plan_t plan, const float* d_f_in, float* d_f_out, const float* d_g, float tau,
+                         float lam, float eps, int32_t nonneg, float* d_delta, void* stream);
+
+/*
  * pat_plan_sync_status — synchronise the stream and report a device-side
  * error recorded by a bounded wait in a persistent launch (PAT_ERR_TIMEOUT),
  * clearing it.  Returns PAT_OK when none was recorded.
@@ -221,7 +237,7 @@ pat_status_t pat_plan_sync_status(pat_plan_t plan, void* stream);
  */
 typedef enum {
     PAT_K_CIRCMEAN = 0, PAT_K_ABEL_FWD = 1, PAT_K_ABEL_ADJ = 2, PAT_K_ADJ_GATHER = 3,
-    PAT_K_TV = 4, PAT_K_RESIDUAL = 5, PAT_K_DESCENT = 6, PAT_K_COUNT = 7
+    PAT_K_TV = 4, PAT_K_RESIDUAL = 5, PAT_K_DESCENT = 6, PAT_K_TV_UPDATE = 7, PAT_K_COUNT = 8
 } pat_kernel_kind_t;
 pat_status_t pat_plan_set_timing(pat_plan_t plan, int32_t enable);
 pat_status_t pat_plan_kernel_times(pat_plan_t plan, double* total_ms, int64_t* launches, int32_t n_kinds);

@@ -222,6 +222,20 @@ class PatPlan:
             ctypes.c_float(lam), 1 if nonneg else 0, ctypes.c_void_p(delta.data_ptr() if delta is not None else 0),
             _stream_ptr(stream, self.device)))
 
+    def tv_step(self, f_in: torch.Tensor, f_out: torch.Tensor, g: torch.Tensor, tau: float, lam: float, eps: float,
+                nonneg: bool = True, delta: torch.Tensor | None = None, stream=None) -> None:
+        """One projected-gradient TV iteration (Eq. (4)) into f_out (fused kernels)."""
+        self._check(f_in, self.f_elems, torch.float32, "f_in")
+        self._check(f_out, self.f_elems, torch.float32, "f_out")
+        self._check(g, self.g_elems, torch.float32, "g")
+        if delta is not None:
+            self._check(delta, 2 * len(self.geoms), torch.float32, "delta")
+        _lib.check("pat_tv_step", self._lib.pat_tv_step(
+            self._h, ctypes.c_void_p(f_in.data_ptr()), ctypes.c_void_p(f_out.data_ptr()),
+            ctypes.c_void_p(g.data_ptr()), ctypes.c_float(tau), ctypes.c_float(lam), ctypes.c_float(eps),
+            1 if nonneg else 0, ctypes.c_void_p(delta.data_ptr() if delta is not None else 0),
+            _stream_ptr(stream, self.device)))
+
     def set_timing(self, enable: bool) -> None:
         """Bracket every kernel launch of this plan with CUDA events."""
         _lib.check("pat_plan_set_timing", self._lib.pat_plan_set_timing(self._h, 1 if enable else 0))

@@ -54,7 +54,9 @@ __device__ __forceinline__ void stage_slice(float* sP, const float* src, int pit
 }
 } // namespace
 
-__global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel_fwd(DevPlan dp, float* __restrict__ g)
+// gsub (nullable): when given, the output is A f - gsub (the data residual).
+__global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel_fwd(DevPlan dp, float* __restrict__ g,
+                                                                 const float* __restrict__ gsub)
 {
     extern __shared__ __align__(128) float smem_f[];
     float* sP = smem_f;                           // [kAbelChunk][32]
@@ -96,11 +98,15 @@ __global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel_fwd(DevPlan dp, flo
     const float4 s = reduce_warps(acc, red);
     if (w == 0 && kk < n_t) {
         const float sc = in.inv_K;
-        float* out = g + in.g_off + kk;
-        if (t.j0 + 0 < in.n_det) out[(size_t)(t.j0 + 0) * n_t] = s.x * sc;
-        if (t.j0 + 1 < in.n_det) out[(size_t)(t.j0 + 1) * n_t] = s.y * sc;
-        if (t.j0 + 2 < in.n_det) out[(size_t)(t.j0 + 2) * n_t] = s.z * sc;
-        if (t.j0 + 3 < in.n_det) out[(size_t)(t.j0 + 3) * n_t] = s.w * sc;
+        const size_t o = in.g_off + kk;
+        float* out = g + o;
+        const float r[4] = {s.x * sc, s.y * sc, s.z * sc, s.w * sc};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (t.j0 + i >= in.n_det) break;
+            const size_t jo = (size_t)(t.j0 + i) * n_t;
+            out[jo] = gsub ? r[i] - gsub[o + jo] : r[i];
+        }
     }
 }
 
@@ -158,12 +164,12 @@ static cudaError_t set_abel_smem(const void* fn, int bytes)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st)
+cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st, const float* gsub)
 {
     if (dp.n_fwd_tiles == 0) return cudaSuccess;
     cudaError_t e = set_abel_smem(reinterpret_cast<const void*>(k_abel_fwd), dp.abel_smem_bytes);
     if (e != cudaSuccess) return e;
-    k_abel_fwd<<<dp.n_fwd_tiles, kAbelWarps * kWarp, dp.abel_smem_bytes, st>>>(dp, g);
+    k_abel_fwd<<<dp.n_fwd_tiles, kAbelWarps * kWarp, dp.abel_smem_bytes, st>>>(dp, g, gsub);
     return cudaGetLastError();
 }
 

@@ -265,6 +265,31 @@ pat_status_t pat_descent_step(pat_plan_t h, float* d_f, const float* d_adj, cons
     }));
 }
 
+pat_status_t pat_tv_step(pat_plan_t h, const float* d_f_in, float* d_f_out, const float* d_g, float tau, float lam,
+                         float eps, int32_t nonneg, float* d_delta, void* stream)
+{
+    Plan* p = lookup(h);
+    if (!p) return PAT_ERR_BAD_PLAN;
+    if (p->dp.bf16) return PAT_ERR_UNSUPPORTED;
+    if (!d_f_in || !d_f_out || !d_g || !aligned16(d_f_in) || !aligned16(d_f_out) || !aligned16(d_g))
+        return PAT_ERR_INVALID_ARG;
+    if (d_f_in == d_f_out) return PAT_ERR_INVALID_ARG;
+    if (!std::isfinite(tau) || !std::isfinite(lam) || !(eps > 0.f) || !std::isfinite(eps)) return PAT_ERR_INVALID_ARG;
+    DeviceScope ds(p->device);
+    if (!ds.ok) return PAT_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const DevPlan& dp = p->dp;
+    cudaError_t e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return launch_circmean(dp, d_f_in, st); });
+    if (e == cudaSuccess)
+        e = timed(*p, PAT_K_ABEL_FWD, st, [&] { return launch_abel_fwd(dp, p->d_resid, st, d_g); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, p->d_resid, st); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return launch_adjoint_cells(dp, st); });
+    if (e == cudaSuccess)
+        e = timed(*p, PAT_K_TV_UPDATE, st,
+                  [&] { return launch_tv_update(dp, d_f_in, d_f_out, tau, lam, eps, nonneg, d_delta, st); });
+    return cuda_status(e);
+}
+
 pat_status_t pat_plan_sync_status(pat_plan_t h, void* stream)
 {
     Plan* p = lookup(h);

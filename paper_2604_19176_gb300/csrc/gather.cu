@@ -283,7 +283,7 @@ cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* co
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_gather(const DevPlan& dp, void* f, cudaStream_t st)
+cudaError_t launch_adjoint_cells(const DevPlan& dp, cudaStream_t st)
 {
     if (dp.adj_mode == 1) {
         if (dp.n_list_items == 0) return cudaSuccess;
@@ -292,7 +292,12 @@ cudaError_t launch_adjoint_gather(const DevPlan& dp, void* f, cudaStream_t st)
         if (dp.n_cell_items == 0) return cudaSuccess;
         k_adj_cells<<<dp.cell_blocks, 256, 0, st>>>(dp);
     }
-    cudaError_t e = cudaGetLastError();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_gather(const DevPlan& dp, void* f, cudaStream_t st)
+{
+    cudaError_t e = launch_adjoint_cells(dp, st);
     if (e != cudaSuccess) return e;
     if (dp.bf16) k_adj_combine<__nv_bfloat16><<<dp.n_img_tiles, 256, 0, st>>>(dp, static_cast<__nv_bfloat16*>(f));
     else k_adj_combine<float><<<dp.n_img_tiles, 256, 0, st>>>(dp, static_cast<float*>(f));

@@ -11,9 +11,15 @@ namespace patgpu {
 constexpr int kCircThreads = 512;   // threads per circular-mean CTA (16 warps)
 
 cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st);
-cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st);
+cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st, const float* gsub = nullptr);
 cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st);
 cudaError_t launch_adjoint_gather(const DevPlan& dp, void* f, cudaStream_t st);
+// Adjoint cell sums only (no combine), for the fused TV step.
+cudaError_t launch_adjoint_cells(const DevPlan& dp, cudaStream_t st);
+// Fused combine + TV gradient + projected update:
+// f_out = [f_in - tau (A^T r + lam grad TV_eps(f_in))]_+ ; delta as pat_descent_step.
+cudaError_t launch_tv_update(const DevPlan& dp, const float* f_in, float* f_out, float tau, float lam, float eps,
+                             int nonneg, float* delta, cudaStream_t st);
 cudaError_t launch_tv(const DevPlan& dp, const float* f, float eps, float* grad, float* value, cudaStream_t st);
 cudaError_t launch_residual(const float* a, const float* b, float* r, float scale, int64_t n, cudaStream_t st);
 cudaError_t launch_descent(const DevPlan& dp, float* f, const float* adj, const float* tvg, float tau, float lam,

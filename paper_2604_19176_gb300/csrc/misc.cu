@@ -100,6 +100,75 @@ __global__ void __launch_bounds__(256) k_descent(DevPlan dp, float* __restrict__
     }
 }
 
+// Fused last stage of one projected-gradient TV iteration (Eq. (4)): the
+// adjoint value of each pixel from its four cells' corner sums (as
+// k_adj_combine), the TV gradient (as k_tv) and the projected update, written
+// to a second buffer because the stencil reads the neighbours' old values.
+__global__ void __launch_bounds__(256) k_tv_update(DevPlan dp, const float* __restrict__ f, float* __restrict__ fout,
+                                                   float tau, float lam, float eps, int nonneg,
+                                                   float* __restrict__ part)
+{
+    __shared__ float red[8];
+    const ImgTile t = dp.img_tiles[blockIdx.x];
+    const InstDev in = dp.inst[t.inst];
+    const int n = in.n;
+    const float* fi = f + in.f_off;
+    const int j = t.x0 + (threadIdx.x & 31), i = t.y0 + (threadIdx.x >> 5);
+    float d2 = 0.f, n2 = 0.f;
+    if (i < n && j < n) {
+        // A^T r at pixel (j, i): corner sums of cells (j,i), (j-1,i), (j,i-1), (j-1,i-1)
+        const int w = n + 1;
+        const float4* z = dp.zbuf + in.z_off;
+        float s = 0.f;
+        for (int g = 0; g < dp.adj_groups; ++g) {
+            const float4* zg = z + (size_t)g * w * w;
+            s += __ldg(&zg[(size_t)(i + 1) * w + j + 1].x) + __ldg(&zg[(size_t)(i + 1) * w + j].y) +
+                 __ldg(&zg[(size_t)i * w + j + 1].z) + __ldg(&zg[(size_t)i * w + j].w);
+        }
+        const float adj = s * in.inv_K;
+        const float eps2 = eps * eps;
+        float dx, dy;
+        const float st = tv_term(fi, n, i, j, eps2, dx, dy);
+        float gtv = -(dx + dy) / st;
+        if (j > 0) {
+            float dxl, dyl;
+            const float sl = tv_term(fi, n, i, j - 1, eps2, dxl, dyl);
+            gtv += dxl / sl;
+        }
+        if (i > 0) {
+            float dxu, dyu;
+            const float su = tv_term(fi, n, i - 1, j, eps2, dxu, dyu);
+            gtv += dyu / su;
+        }
+        const float old = fi[(size_t)i * n + j];
+        float nv = fmaf(-tau, fmaf(lam, gtv, adj), old);
+        if (nonneg) nv = fmaxf(nv, 0.f);
+        fout[in.f_off + (size_t)i * n + j] = nv;
+        d2 = (nv - old) * (nv - old);
+        n2 = nv * nv;
+    }
+    if (part) {
+        const float s0 = block_sum<256>(d2, red);
+        const float s1 = block_sum<256>(n2, red);
+        if (threadIdx.x == 0) {
+            part[2 * blockIdx.x] = s0;
+            part[2 * blockIdx.x + 1] = s1;
+        }
+    }
+}
+
+cudaError_t launch_tv_update(const DevPlan& dp, const float* f_in, float* f_out, float tau, float lam, float eps,
+                             int nonneg, float* delta, cudaStream_t st)
+{
+    if (dp.n_img_tiles == 0) return cudaSuccess;
+    k_tv_update<<<dp.n_img_tiles, 256, 0, st>>>(dp, f_in, f_out, tau, lam, eps, nonneg,
+                                                delta ? dp.tv_partial : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !delta) return e;
+    k_tile_sums<<<dp.n_inst, 32, 0, st>>>(dp, dp.tv_partial, 2, delta);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tv(const DevPlan& dp, const float* f, float eps, float* grad, float* value, cudaStream_t st)
 {
     if (dp.n_img_tiles == 0) return cudaSuccess;

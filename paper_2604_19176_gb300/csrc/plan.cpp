@@ -637,7 +637,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const int64_t o_arr = o_tvp + tv_parts;
     const int64_t o_ctr = o_arr + arrive_total;
     const int64_t n_ctr = kCircQueueBase + 2 * n_band_tasks;
-    const int64_t z_float_off = ((o_ctr + n_ctr + 63) / 64) * 64;
+    const int64_t o_res = ((o_ctr + n_ctr + 63) / 64) * 64;   // data residual of pat_tv_step
+    const int64_t z_float_off = ((o_res + P.g_offsets[n_inst] + 63) / 64) * 64;
     P.work_floats = z_float_off + 4 * z_total;
     if (cudaMalloc(&P.d_work, sizeof(float) * std::max<int64_t>(P.work_floats, 1)) != cudaSuccess) {
         P.d_work = nullptr;
@@ -673,6 +674,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.tv_partial = P.d_work + o_tvp;
     dp.slot_arrivals = reinterpret_cast<int32_t*>(P.d_work + o_arr);
     dp.work_counters = reinterpret_cast<int32_t*>(P.d_work + o_ctr);
+    P.d_resid = P.d_work + o_res;
     P.d_counters = reinterpret_cast<int32_t*>(P.d_work + o_arr);
     P.counters_bytes = (size_t)(o_ctr + n_ctr - o_arr) * 4;
     dp.zbuf = reinterpret_cast<float4*>(P.d_work + z_float_off);

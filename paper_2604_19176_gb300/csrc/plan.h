@@ -30,6 +30,7 @@ struct Plan {
     int32_t* d_counters = nullptr;     // arrival counters + work queues (zero between calls)
     size_t counters_bytes = 0;
     void* d_lists = nullptr;           // adjoint sample lists (list mode)
+    float* d_resid = nullptr;          // data residual of the fused TV step (inside d_work)
     int code_bits_max = 0;             // bits of a packed (j, m, q) sample code, largest instance
     int64_t list_budget_bytes = 24ll << 30;
     int fwd_smem = 0;

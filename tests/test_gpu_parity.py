@@ -214,3 +214,27 @@ def test_plan_errors(cuda_dev):
     with pytest.raises(ValueError):
         plan.forward(torch.zeros(15, 16, device=cuda_dev))
     plan.close()
+
+
+def test_fused_tv_step_matches_separate_calls(cuda_dev):
+    """pat_tv_step equals pat_forward, pat_residual, pat_adjoint, pat_tv_grad
+    and pat_descent_step in sequence (same arithmetic, fewer kernels)."""
+    g = Geometry(64, 32, 0.2, math.pi, 96, 2.0, 128)
+    plan = PatPlan(g, device=cuda_dev)
+    f0 = torch.tensor(np.abs(inputs.random_image(64, seed=41)), dtype=torch.float32, device=cuda_dev)
+    data = torch.tensor(inputs.random_data(32, 96, seed=42), dtype=torch.float32, device=cuda_dev)
+    tau, lam, eps = 0.05, 0.3, 1e-2
+    # separate calls
+    f_a = f0.clone()
+    r = plan.residual(plan.forward(f_a), data)
+    adj = plan.adjoint(r)
+    _, tvg = plan.tv_grad(f_a, eps)
+    da = torch.zeros(2, device=cuda_dev)
+    plan.descent_step(f_a, adj, tvg, tau, lam, nonneg=True, delta=da)
+    # fused
+    f_b = torch.empty_like(f0)
+    db = torch.zeros(2, device=cuda_dev)
+    plan.tv_step(f0, f_b, data, tau, lam, eps, nonneg=True, delta=db)
+    torch.cuda.synchronize()
+    assert torch.equal(f_a, f_b)
+    assert torch.equal(da, db)
