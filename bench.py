@@ -237,7 +237,7 @@ def main():
     from paper_2604_19176_gb300 import PatPlan, inputs
 
     wl, g, f_true = make_inputs(seed_offset=rank)
-    plan = PatPlan(g, device=dev)
+    plan = PatPlan(g, device=dev, tune=1)  # autotuned tile shapes (timed at plan creation)
     info = plan.info()
     stream = torch.cuda.current_stream(dev)
 
@@ -374,6 +374,8 @@ def main():
                            "step": "pat_tv_step: A f, residual, A^T r, TV gradient, projected update"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * n_steps,
+                "tile_shape": {k: info[k] for k in ("m_lanes", "q_piece", "band_rows", "bands_max", "adj_groups",
+                                                    "adj_mode")},
                 "samples_per_application": samples, "sample_slots": info["sample_slots"],
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
         print(json.dumps(line), flush=True)

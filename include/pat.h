@@ -92,8 +92,9 @@ typedef struct {
 typedef struct {
     int32_t image_dtype; /* pat_dtype_t: storage of f in pat_forward / pat_adjoint           */
     int32_t schedule;    /* pat_schedule_t                                                   */
-    int32_t tune;        /* 0 = built-in tile shapes, 1 = time candidates at creation (needs  */
-                         /*     a stream; synchronises it), 2 = use tile fields below         */
+    int32_t tune;        /* 0 = tile fields below (0 = built-in), 1 = time candidate tile     */
+                         /*     shapes at creation on these geometries (temporary device      */
+                         /*     buffers, synchronises the stream; cached per process), 2 = 0  */
     int32_t m_lanes;     /* radii per warp in the circular-mean kernel (32, 16 or 8); 0=auto */
     int32_t q_piece;     /* max angular nodes per work unit (multiple of 4); 0 = auto        */
     int32_t band_rows;   /* max image rows per shared-memory band; 0 = auto                  */

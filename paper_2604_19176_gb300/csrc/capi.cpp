@@ -124,7 +124,6 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
     if (opt.schedule != PAT_SCHED_STAGED && opt.schedule != PAT_SCHED_PERSISTENT) return PAT_ERR_INVALID_ARG;
     if (opt.schedule == PAT_SCHED_PERSISTENT) return PAT_ERR_UNSUPPORTED;
     if (opt.tune < 0 || opt.tune > 2) return PAT_ERR_INVALID_ARG;
-    if (opt.tune == 1) return PAT_ERR_UNSUPPORTED;
     if (opt.m_lanes == 0) opt.m_lanes = 32;
     if (opt.m_lanes != 32 && opt.m_lanes != 16 && opt.m_lanes != 8) return PAT_ERR_INVALID_ARG;
     if (opt.q_piece == 0) opt.q_piece = 128;
@@ -136,20 +135,30 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
     for (int i = 0; i < n_instances; ++i)
         if (!valid_geometry(geoms[i], bf16)) return PAT_ERR_INVALID_ARG;
 
-    Plan* p = new (std::nothrow) Plan();
-    if (!p) return PAT_ERR_OOM;
+    Plan* p = nullptr;
     pat_status_t s;
-    try {
-        s = build_plan(*p, geoms, n_instances, opt, static_cast<cudaStream_t>(stream));
-    } catch (const std::bad_alloc&) {
-        s = PAT_ERR_OOM;
-    } catch (...) {
-        s = PAT_ERR_INVALID_ARG;
-    }
-    if (s != PAT_OK) {
-        free_plan_memory(*p);
-        delete p;
-        return s;
+    if (opt.tune == 1) {
+        try {
+            s = autotune_plan(&p, geoms, n_instances, opt, static_cast<cudaStream_t>(stream));
+        } catch (const std::bad_alloc&) {
+            s = PAT_ERR_OOM;
+        }
+        if (s != PAT_OK) return s;
+    } else {
+        p = new (std::nothrow) Plan();
+        if (!p) return PAT_ERR_OOM;
+        try {
+            s = build_plan(*p, geoms, n_instances, opt, static_cast<cudaStream_t>(stream));
+        } catch (const std::bad_alloc&) {
+            s = PAT_ERR_OOM;
+        } catch (...) {
+            s = PAT_ERR_INVALID_ARG;
+        }
+        if (s != PAT_OK) {
+            free_plan_memory(*p);
+            delete p;
+            return s;
+        }
     }
     {
         std::lock_guard<std::mutex> lk(g_mu);

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <queue>
 #include <thread>
@@ -101,7 +102,25 @@ void abel_weights_gl(double tau, int n_r, const std::vector<double>& gx, const s
 // Abel-plus-midpoint-derivative matrix P (n_t x (n_t + 2)), FP64 -> FP32:
 // p(t_k) = (Q(t_k + Delta/2) - Q(t_k - Delta/2)) / Delta with Q the Abel
 // integral of the piecewise-linear circular mean; Delta cancels.
+std::vector<float> build_abel_matrix_uncached(int n_t);
+
+// Abel matrices are geometry independent (only n_t matters): cache them.
 std::vector<float> build_abel_matrix(int n_t)
+{
+    static std::mutex mu;
+    static std::map<int, std::vector<float>> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(n_t);
+        if (it != cache.end()) return it->second;
+    }
+    std::vector<float> P = build_abel_matrix_uncached(n_t);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[n_t] = P;
+    return P;
+}
+
+std::vector<float> build_abel_matrix_uncached(int n_t)
 {
     const int n_r = n_t + 2;
     std::vector<double> gx, gw;

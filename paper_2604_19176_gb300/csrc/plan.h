@@ -48,4 +48,9 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                         cudaStream_t st);
 void free_plan_memory(Plan& P);
 
+// Builds the plan with the fastest of a set of candidate tile shapes, timed on
+// the plan's geometries (tune = 1); results are cached per process.
+pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, const pat_options_t& opt,
+                           cudaStream_t st);
+
 } // namespace patgpu

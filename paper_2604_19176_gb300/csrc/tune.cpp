@@ -1,0 +1,202 @@
+// tune.cpp — autotuner for the tile shapes of a plan.
+//
+// Candidates for the circular-mean kernel (radii per warp, angles per unit,
+// rows per shared-memory band) are timed on the plan's own geometries with
+// CUDA events, then candidates for the adjoint gather (detector groups) with
+// the best forward shape; the fastest plan is kept.  Results are cached per
+// process by geometry list and image dtype, so a second plan with the same
+// geometries skips the search.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "plan.h"
+
+namespace patgpu {
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, pat_options_t> g_tune_cache;
+
+std::string tune_key(const pat_geometry_t* geoms, int n, const pat_options_t& opt, int device)
+{
+    std::string k(reinterpret_cast<const char*>(geoms), sizeof(pat_geometry_t) * (size_t)n);
+    k.append(reinterpret_cast<const char*>(&opt.image_dtype), sizeof(int32_t));
+    k.append(reinterpret_cast<const char*>(&device), sizeof(int));
+    return k;
+}
+
+template <typename F>
+float time_ms(cudaStream_t st, int warm, int reps, F&& fn)
+{
+    for (int i = 0; i < warm; ++i)
+        if (fn() != cudaSuccess) return -1.f;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    float ms = -1.f;
+    bool ok = cudaEventRecord(a, st) == cudaSuccess;
+    for (int i = 0; i < reps && ok; ++i) ok = fn() == cudaSuccess;
+    if (ok && cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+        ms /= reps;
+    else
+        ms = -1.f;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+Plan* try_build(const pat_geometry_t* geoms, int n, const pat_options_t& opt, cudaStream_t st)
+{
+    Plan* p = new (std::nothrow) Plan();
+    if (!p) return nullptr;
+    pat_status_t s;
+    try {
+        s = build_plan(*p, geoms, n, opt, st);
+    } catch (...) {
+        s = PAT_ERR_OOM;
+    }
+    if (s != PAT_OK) {
+        free_plan_memory(*p);
+        delete p;
+        return nullptr;
+    }
+    return p;
+}
+
+void drop(Plan* p)
+{
+    if (!p) return;
+    free_plan_memory(*p);
+    delete p;
+}
+
+} // namespace
+
+pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, const pat_options_t& opt_in,
+                           cudaStream_t st)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PAT_ERR_CUDA;
+    pat_options_t opt = opt_in;
+    opt.tune = 0;
+    const std::string key = tune_key(geoms, n_inst, opt, dev);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            Plan* p = try_build(geoms, n_inst, it->second, st);
+            if (!p) return PAT_ERR_CUDA;
+            *out = p;
+            return PAT_OK;
+        }
+    }
+    const bool bf16 = opt.image_dtype == PAT_BF16;
+    int64_t f_elems = 0, g_elems = 0;
+    int n_max = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        f_elems += (int64_t)geoms[i].n * geoms[i].n;
+        g_elems += (int64_t)geoms[i].n_det * geoms[i].n_t;
+        n_max = std::max(n_max, geoms[i].n);
+    }
+    void* d_f = nullptr;
+    float* d_g = nullptr;
+    if (cudaMalloc(&d_f, (size_t)f_elems * (bf16 ? 2 : 4)) != cudaSuccess) {
+        cudaGetLastError();
+        return PAT_ERR_OOM;
+    }
+    if (cudaMalloc(&d_g, (size_t)g_elems * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_f);
+        return PAT_ERR_OOM;
+    }
+    cudaMemsetAsync(d_f, 0, (size_t)f_elems * (bf16 ? 2 : 4), st);
+    cudaMemsetAsync(d_g, 0, (size_t)g_elems * 4, st);
+
+    // ---- forward candidates ---------------------------------------------
+    const int W = bf16 ? band_pitch_bf16(n_max) : band_pitch_f32(n_max);
+    const int esize = bf16 ? 2 : 4;
+    const int max_rows = (227 * 1024) / (W * esize);
+    std::vector<int> rows_cands = {0};
+    for (int nb : {1, 2, 4, 6}) {
+        const int rows = (n_max + 1 + nb - 1) / nb + 1;
+        if (rows <= max_rows && rows >= 3) rows_cands.push_back(rows);
+    }
+    Plan* best = nullptr;
+    float best_ms = 1e30f;
+    pat_options_t best_opt = opt;
+    const bool large = f_elems > (1 << 20);   // keep the search short on big plans
+    const std::vector<int> ml_c = large ? std::vector<int>{32} : std::vector<int>{32, 16};
+    const std::vector<int> qp_c = large ? std::vector<int>{128, 256} : std::vector<int>{64, 128, 256};
+    for (int ml : ml_c) {
+        for (int qp : qp_c) {
+            for (int rows : rows_cands) {
+                pat_options_t o = opt;
+                o.m_lanes = ml;
+                o.q_piece = qp;
+                o.band_rows = rows;
+                o.adj_mode = 2;      // the adjoint is tuned below; skip list building here
+                o.adj_groups = 1;
+                Plan* p = try_build(geoms, n_inst, o, st);
+                if (!p) continue;
+                const float ms = time_ms(st, 2, 5, [&] {
+                    cudaError_t e = launch_circmean(p->dp, d_f, st);
+                    return e == cudaSuccess ? launch_abel_fwd(p->dp, d_g, st) : e;
+                });
+                drop(p);
+                if (ms > 0.f && ms < best_ms) {
+                    best_ms = ms;
+                    best_opt = o;
+                }
+            }
+        }
+    }
+    // ---- adjoint candidates (with the best forward shape) ------------------
+    best_ms = 1e30f;
+    pat_options_t fwd_opt = best_opt;
+    std::vector<std::pair<int, int>> adj_cands = {{opt.adj_mode, 0}};
+    for (int gcount : {1, 2, 4, 8}) adj_cands.push_back({opt.adj_mode, gcount});
+    for (auto& ac : adj_cands) {
+        pat_options_t o = fwd_opt;
+        o.adj_mode = ac.first;
+        o.adj_groups = ac.second;
+        Plan* p = try_build(geoms, n_inst, o, st);
+        if (!p) continue;
+        const float ms = time_ms(st, 2, 5, [&] {
+            cudaError_t e = launch_abel_adj(p->dp, d_g, st);
+            return e == cudaSuccess ? launch_adjoint_gather(p->dp, d_f, st) : e;
+        });
+        if (ms > 0.f && ms < best_ms) {
+            best_ms = ms;
+            drop(best);
+            best = p;
+            best_opt = o;
+        } else {
+            drop(p);
+        }
+    }
+    cudaFree(d_f);
+    cudaFree(d_g);
+    if (!best) return PAT_ERR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best_opt;
+    }
+    best->opt.tune = 1;
+    *out = best;
+    return PAT_OK;
+}
+
+} // namespace patgpu
