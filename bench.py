@@ -217,6 +217,134 @@ def reference_arm(args):
 
 
 # --------------------------------------------------------------------------
+# secondary workloads (reported under "extras"; not the headline metric)
+# --------------------------------------------------------------------------
+def _time_steps(fn, stream, flush, steps, warmup=3):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ms.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.mean(x.elapsed_time(y) for x, y in ms)
+
+
+def run_extras(dev, flush, with_oracle: bool = True) -> dict:
+    import torch
+
+    from paper_2604_19176_gb300 import PatPlan, inputs, workloads
+    from paper_2604_19176_gb300.graphs import GraphedOperator
+    from paper_2604_19176_gb300.recon import UNet, pat_apply, tv_value
+
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    # DIP iteration: U-Net (4 levels, 32 base channels, FP32, no TF32) on the
+    # 256^2 geometry, loss ||A f - g||^2 + 1e-4 TV(f), one Adam step at 1e-4.
+    wl = workloads.vessel256_half()
+    g = wl.geometries[0]
+    plan = PatPlan(g, device=dev, tune=1)
+    f_true = torch.tensor(wl.phantoms()[0], dtype=torch.float32, device=dev)
+    data = plan.forward(f_true)
+    torch.cuda.synchronize()
+    data = torch.tensor(inputs.add_noise(data.double().cpu().numpy(), 0.05, seed=78), dtype=torch.float32,
+                        device=dev)
+    z = torch.tensor(inputs.dip_input(32, g.n, seed=3), dtype=torch.float32, device=dev)
+    torch.manual_seed(0)
+    net = UNet(in_ch=32, base=32).to(dev)
+    opt = torch.optim.Adam(net.parameters(), lr=1e-4)
+
+    def dip_iter():
+        opt.zero_grad(set_to_none=True)
+        f = net(z).reshape(g.n, g.n)
+        r = pat_apply(f, plan) - data
+        loss = (r * r).sum() + 1e-4 * tv_value(f, plan, 1e-3).sum()
+        loss.backward()
+        opt.step()
+
+    it_ms = _time_steps(dip_iter, stream, flush, 20, warmup=5)
+    plan.set_timing(True)
+    for _ in range(10):
+        dip_iter()
+    torch.cuda.synchronize()
+    plan.set_timing(False)
+    kt = plan.kernel_times()
+    op_ms = sum(v[0] for v in kt.values()) / 10
+    out["dip_vessel256"] = {"iters_per_s": 1000.0 / it_ms, "ms_per_iter": it_ms, "operator_ms_per_iter": op_ms,
+                            "operator_share": op_ms / it_ms,
+                            "config": "U-Net 4 levels / 32 base channels FP32 (TF32 off), z ~ N(0, 0.1^2) "
+                                      "1x32x256x256, Adam lr 1e-4, loss ||Af-g||^2 + 1e-4 TV, 5% noise"}
+
+    # 512^2 variant, fused TV step
+    wl = workloads.vessel512_half()
+    g = wl.geometries[0]
+    p512 = PatPlan(g, device=dev, tune=1)
+    d512 = p512.forward(torch.tensor(wl.phantoms()[0], dtype=torch.float32, device=dev))
+    fa, fb = torch.zeros(g.n, g.n, device=dev), torch.zeros(g.n, g.n, device=dev)
+    ms512 = _time_steps(lambda: p512.tv_step(fa, fb, d512, 1e-4, 1e-3, 1e-3), stream, flush, 100)
+    out["vessel512_half"] = {"apps_per_s": 1000.0 / ms512, "ms_per_step": ms512, "samples": p512.info()["samples"]}
+    del p512
+
+    # BF16 image storage vs FP32 at 256^2 (forward + adjoint), errors vs the FP64 oracle
+    wl = workloads.vessel256_half()
+    g = wl.geometries[0]
+    f_np = wl.phantoms()[0]
+    rng_g = inputs.random_data(g.n_det, g.n_t, seed=5)
+    res = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        pp = PatPlan(g, device=dev, image_dtype=dt, tune=1)
+        ft = torch.tensor(f_np, dtype=dt, device=dev)
+        gt = torch.tensor(rng_g, dtype=torch.float32, device=dev)
+        go, fo = torch.empty(pp.data_shape(), device=dev), torch.empty(pp.image_shape(), dtype=dt, device=dev)
+
+        def fa_step():
+            pp.forward(ft, out=go)
+            pp.adjoint(gt, out=fo)
+
+        res[name] = {"apps_per_s": 1000.0 / _time_steps(fa_step, stream, flush, 100)}
+        fa_step()
+        torch.cuda.synchronize()
+        res[name]["_fwd"] = go.double().cpu().numpy()
+        res[name]["_adj"] = fo.double().cpu().numpy()
+    if with_oracle:
+        import oracle as O
+
+        O.set_threads(os.cpu_count() or 1)
+        og = O.Geometry(g.n, g.n_det, g.arc_start, g.arc_span, g.n_t, g.t_max, g.n_angles)
+        ref_f = O.forward(og, f_np)
+        ref_a = O.adjoint(og, rng_g.astype(np.float32).astype(np.float64))
+        for name in res:
+            res[name]["rel_l2_fwd_vs_fp64"] = float(np.linalg.norm(res[name]["_fwd"] - ref_f) / np.linalg.norm(ref_f))
+            res[name]["rel_l2_adj_vs_fp64"] = float(np.linalg.norm(res[name]["_adj"] - ref_a) / np.linalg.norm(ref_a))
+        O.set_threads(1)
+    for name in res:
+        res[name].pop("_fwd")
+        res[name].pop("_adj")
+    out["storage_256"] = res
+
+    # 64 uneven instances, forward + adjoint replayed from one CUDA graph
+    geoms = list(workloads.batch64_uneven().geometries)
+    pb = PatPlan(geoms, device=dev, tune=1)
+    op = GraphedOperator(pb)
+    op.f_in.copy_(torch.rand(pb.image_shape(), device=dev))
+    op.g_in.copy_(torch.rand(pb.data_shape(), device=dev))
+    msb = _time_steps(op.replay, stream, flush, 20)
+    out["batch64_uneven"] = {"instances_per_s": 64 * 1000.0 / msb, "ms_per_batch": msb,
+                             "samples": pb.info()["samples"], "graph": "forward + adjoint, one replay"}
+    del op, pb
+    return out
+
+
+# --------------------------------------------------------------------------
 def main():
     args = parse()
     if args.impl == "reference":
@@ -364,6 +492,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile:
         cpu = cpu_oracle_timing(g, f_true)
 
+    extras = None
+    if rank == 0 and not args.no_extras and not args.profile:
+        extras = run_extras(dev, flush, with_oracle=(world == 1))
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -377,7 +509,8 @@ def main():
                 "tile_shape": {k: info[k] for k in ("m_lanes", "q_piece", "band_rows", "bands_max", "adj_groups",
                                                     "adj_mode")},
                 "samples_per_application": samples, "sample_slots": info["sample_slots"],
-                "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
+                "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
+                "extras": extras}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
