@@ -23,16 +23,15 @@ namespace patgpu {
 namespace {
 
 // One bilinear sample of the staged band; 0 for samples whose cell lies
-// outside the band (they belong to another band or to no pixel).
+// outside the band (they belong to another band or to no pixel).  s points at
+// the detector's integer cell (Ui, Vi); cells and bounds are relative to it.
 template <typename T>
-__device__ __forceinline__ float sample(const T* __restrict__ s, int W, float rho, float2 cs, float U, float V,
+__device__ __forceinline__ float sample(const T* __restrict__ s, int W, float mf, float4 r, float Uf, float Vf,
                                         float ulo, float uhi, float vlo, float vhi)
 {
-    const float u = __fmaf_rn(rho, cs.x, U);
-    const float v = __fmaf_rn(rho, cs.y, V);
-    const float fu = floorf(u), fv = floorf(v);
+    const float fu = cell_rel(mf, r.x, Uf), fv = cell_rel(mf, r.y, Vf);
     const bool ok = (fu >= ulo) & (fu <= uhi) & (fv >= vlo) & (fv <= vhi);
-    const float a = __fsub_rn(u, fu), b = __fsub_rn(v, fv);
+    const float a = cell_frac(mf, r.x, r.z, Uf, fu), b = cell_frac(mf, r.y, r.w, Vf, fv);
     const T* p = s + (__float2int_rz(fv) * W + __float2int_rz(fu));
     float f00 = 0.f, f10 = 0.f, f01 = 0.f, f11 = 0.f;
     if (ok) {
@@ -112,9 +111,8 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
         const T* sb = s + ((in.c0 - sg.band_lo) * W + in.c0 + CO);
         const float ulo = (float)(-1 - in.c0), uhi = (float)(n - 1 - in.c0);
         const float vlo = (float)(sg.band_lo - in.c0), vhi = (float)(sg.band_hi - 1 - in.c0);
-        const float* detU = dp.detU + in.det_off;
-        const float* detV = dp.detV + in.det_off;
-        const float2* trig = dp.trig + in.trig_off;
+        const float4* det = dp.det + in.det_off;
+        const float4* rays = dp.rays + in.ray_off;
         const Unit* units = dp.units + sg.unit_begin;
         int32_t* queue = dp.work_counters + kCircQueueBase + 2 * sg.queue;
 
@@ -132,19 +130,22 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
             if (u2 < nu) un2 = units[u2];
 
             const int m = un.m0 + ml;
-            const float rho = (float)m * in.delta;
-            const float U = __ldg(detU + un.j), V = __ldg(detV + un.j);
-            const float2* tq = trig + un.q0 + ql;
+            const float mf = (float)m;
+            const float4 d = __ldg(det + un.j);
+            const float Ui = floorf(d.x), Vi = floorf(d.y);
+            const T* sj = sb + (__float2int_rz(Vi) * W + __float2int_rz(Ui));
+            const float ul = ulo - Ui, uh = uhi - Ui, vl = vlo - Vi, vh = vhi - Vi;
+            const float4* tq = rays + un.q0 + ql;
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
             int i = ql;
             for (; i + 3 * QL < un.nq; i += 4 * QL, tq += 4 * QL) {
-                const float2 c0 = __ldg(tq), c1 = __ldg(tq + QL), c2 = __ldg(tq + 2 * QL), c3 = __ldg(tq + 3 * QL);
-                acc0 += sample(sb, W, rho, c0, U, V, ulo, uhi, vlo, vhi);
-                acc1 += sample(sb, W, rho, c1, U, V, ulo, uhi, vlo, vhi);
-                acc2 += sample(sb, W, rho, c2, U, V, ulo, uhi, vlo, vhi);
-                acc3 += sample(sb, W, rho, c3, U, V, ulo, uhi, vlo, vhi);
+                const float4 c0 = __ldg(tq), c1 = __ldg(tq + QL), c2 = __ldg(tq + 2 * QL), c3 = __ldg(tq + 3 * QL);
+                acc0 += sample(sj, W, mf, c0, d.z, d.w, ul, uh, vl, vh);
+                acc1 += sample(sj, W, mf, c1, d.z, d.w, ul, uh, vl, vh);
+                acc2 += sample(sj, W, mf, c2, d.z, d.w, ul, uh, vl, vh);
+                acc3 += sample(sj, W, mf, c3, d.z, d.w, ul, uh, vl, vh);
             }
-            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(sb, W, rho, __ldg(tq), U, V, ulo, uhi, vlo, vhi);
+            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(sj, W, mf, __ldg(tq), d.z, d.w, ul, uh, vl, vh);
             float acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
             for (int o = ML; o < kWarp; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -185,15 +186,16 @@ __global__ void k_count_samples(DevPlan dp, int inst_idx, unsigned long long* __
 {
     const InstDev in = dp.inst[inst_idx];
     const int j = blockIdx.x;
-    const float U = dp.detU[in.det_off + j], V = dp.detV[in.det_off + j];
-    const float2* trig = dp.trig + in.trig_off;
+    const float4 d = dp.det[in.det_off + j];
+    const float Ui = floorf(d.x), Vi = floorf(d.y);
+    const float4* rays = dp.rays + in.ray_off;
     const float lo = (float)(-1 - in.c0), hi = (float)(in.n - 1 - in.c0);
     unsigned long long c = 0;
     for (int m = threadIdx.x; m < in.n_r; m += blockDim.x) {
-        const float rho = (float)m * in.delta;
+        const float mf = (float)m;
         for (int q = 0; q < in.K; ++q) {
-            const float2 cs = trig[q];
-            const float fu = floorf(__fmaf_rn(rho, cs.x, U)), fv = floorf(__fmaf_rn(rho, cs.y, V));
+            const float4 r = rays[q];
+            const float fu = Ui + cell_rel(mf, r.x, d.z), fv = Vi + cell_rel(mf, r.y, d.w);
             c += (fu >= lo && fu <= hi && fv >= lo && fv <= hi) ? 1ull : 0ull;
         }
     }

@@ -36,6 +36,22 @@ template <> struct ImgTraits<__nv_bfloat16> {
 };
 
 // ---------------------------------------------------------------------------
+// Sample coordinates in split form (the coordinate conventions of
+// pat_internal.h).  cell_rel: cell of radius index mf along direction
+// component hi, relative to the detector's integer part, from the detector's
+// fraction f0.  cell_frac: the sample's fraction inside that cell.  Both
+// the forward and the adjoint gathers call exactly these.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float cell_rel(float mf, float hi, float f0)
+{
+    return floorf(__fmaf_rn(mf, hi, f0));
+}
+__device__ __forceinline__ float cell_frac(float mf, float hi, float lo, float f0, float cell)
+{
+    return __fadd_rn(__fmaf_rn(mf, hi, -cell), __fmaf_rn(mf, lo, f0));
+}
+
+// ---------------------------------------------------------------------------
 // TMA (bulk async copy) and mbarrier wrappers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p)

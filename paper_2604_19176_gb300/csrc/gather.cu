@@ -11,8 +11,8 @@
 // samples from rays q whose direction passes within R = sqrt(2)/2 (+ margin)
 // of its centre; each such ray is intersected with the cell (slab test,
 // widened by a margin that covers FP32 rounding) to get the run of radii m
-// that can land in it, and each candidate is re-evaluated with exactly the
-// forward's FP32 expression.  Hits come out in the order (j, q, m).
+// that can land in it, and each candidate's cell is re-evaluated with exactly
+// the forward's split-form expression.  Hits come out in the order (j, q, m).
 //
 // Two ways to run this:
 //   list mode (default when the codes fit): at plan creation the enumeration
@@ -31,21 +31,21 @@ constexpr float kRcell = 0.70710678f + 0.004f;  // half cell diagonal + rounding
 constexpr float kSlabEps = 0.01f;                // slab widening (pixels)
 constexpr float kAngMargin = 1.0e-5f;            // > 5x the atan2_approx error (radians)
 
-// Calls hit(j, m, q, u, v) for every sample (j in j0, j0 + dj, ...) that
-// lands in centred cell (cxf, cyf), in (j, q, m) order; q in [0, K).
+// Calls hit(j, m, q, a, b) for every sample (j in j0, j0 + dj, ...) that
+// lands in centred cell (cxf, cyf), (a, b) its fractions in the cell, in
+// (j, q, m) order; q in [0, K).
 template <typename Hit>
 __device__ __forceinline__ void enumerate_cell(const DevPlan& dp, const InstDev& in, float cxf, float cyf, int j0,
                                                int dj, Hit&& hit)
 {
     const float ccx = cxf + 0.5f, ccy = cyf + 0.5f;
-    const float* detU = dp.detU + in.det_off;
-    const float* detV = dp.detV + in.det_off;
-    const float2* trig = dp.trig + in.trig_off;
-    const float2* rtrig = dp.rtrig + in.rtrig_off;
+    const float4* det = dp.det + in.det_off;
+    const float4* rays = dp.rays + in.ray_off;
+    const float2* rtrig = dp.rtrig + in.ray_off;
     const int K = in.K;
-    const float delta = in.delta;
     for (int j = j0; j < in.n_det; j += dj) {
-        const float U = __ldg(detU + j), V = __ldg(detV + j);
+        const float4 d = __ldg(det + j);
+        const float U = d.x, V = d.y;
         const float du = ccx - U, dv = ccy - V;
         const float rc = sqrtf(fmaf(du, du, dv * dv));
         const int mlo = max(0, (int)ceilf((rc - kRcell) * in.inv_delta));
@@ -61,6 +61,8 @@ __device__ __forceinline__ void enumerate_cell(const DevPlan& dp, const InstDev&
         }
         const float ax0 = (cxf - kSlabEps) - U, ax1 = (cxf + 1.f + kSlabEps) - U;
         const float ay0 = (cyf - kSlabEps) - V, ay1 = (cyf + 1.f + kSlabEps) - V;
+        // the cell relative to the detector's integer part (exact: small integers)
+        const float cxr = cxf - floorf(U), cyr = cyf - floorf(V);
         for (int i = 0; i < qn; ++i) {
             const int q = qlo + i;
             const float2 ri = __ldg(rtrig + q);
@@ -71,12 +73,12 @@ __device__ __forceinline__ void enumerate_cell(const DevPlan& dp, const InstDev&
             const int m0 = max(mlo, (int)ceilf(lo));
             const int m1 = min(mhi, (int)floorf(hi));
             if (m0 > m1) continue;
-            const float2 cs = __ldg(trig + q);
+            const float4 r = __ldg(rays + q);
             for (int m = m0; m <= m1; ++m) {
-                const float rho = (float)m * delta;
-                const float u = __fmaf_rn(rho, cs.x, U);
-                const float v = __fmaf_rn(rho, cs.y, V);
-                if (floorf(u) == cxf && floorf(v) == cyf) hit(j, m, q >= K ? q - K : q, u, v);
+                const float mf = (float)m;
+                if (cell_rel(mf, r.x, d.z) == cxr && cell_rel(mf, r.y, d.w) == cyr)
+                    hit(j, m, q >= K ? q - K : q, cell_frac(mf, r.x, r.z, d.z, cxr),
+                        cell_frac(mf, r.y, r.w, d.w, cyr));
             }
         }
     }
@@ -128,8 +130,8 @@ __global__ void __launch_bounds__(256, 5) k_adj_cells(DevPlan dp)
         const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
         const float* mb = dp.mbar + in.mbar_off;
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        enumerate_cell(dp, in, cxf, cyf, it.group, G, [&](int j, int m, int, float u, float v) {
-            add_corners(z, __fsub_rn(u, cxf), __fsub_rn(v, cyf), __ldg(mb + (size_t)j * in.n_rp + m));
+        enumerate_cell(dp, in, cxf, cyf, it.group, G, [&](int j, int m, int, float a, float b) {
+            add_corners(z, a, b, __ldg(mb + (size_t)j * in.n_rp + m));
         });
         dp.zbuf[in.z_off + (size_t)it.group * (n + 1) * (n + 1) + (size_t)(cy + 1) * (n + 1) + (cx + 1)] = z;
     }
@@ -168,19 +170,17 @@ __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int
 // ---------------------------------------------------------------------------
 namespace {
 __device__ __forceinline__ void list_sample(const uint32_t code, int qb, int mbq, uint32_t mmask, uint32_t qmask,
-                                            const float2* __restrict__ det, const float2* __restrict__ trig,
-                                            const float* __restrict__ mb, int n_rp, float delta, float cxf, float cyf,
-                                            float4& z)
+                                            const float4* __restrict__ det, const float4* __restrict__ rays,
+                                            const float* __restrict__ mb, int n_rp, float cxf, float cyf, float4& z)
 {
     const int j = (int)(code >> mbq), m = (int)((code >> qb) & mmask), q = (int)(code & qmask);
-    const float2 cs = __ldg(trig + q);
-    const float2 UV = __ldg(det + j);
+    const float4 r = __ldg(rays + q);
+    const float4 d = __ldg(det + j);
     const float w = __ldg(mb + j * n_rp + m);
-    const float rho = (float)m * delta;
-    const float u = __fmaf_rn(rho, cs.x, UV.x);
-    const float v = __fmaf_rn(rho, cs.y, UV.y);
-    // the sample lies in this cell, so floor(u) == cxf: a = u - floor(u)
-    add_corners(z, __fsub_rn(u, cxf), __fsub_rn(v, cyf), w);
+    const float mf = (float)m;
+    // the sample lies in this cell, so its relative cell is (cxf, cyf) - floor(U, V)
+    const float cxr = __fsub_rn(cxf, floorf(d.x)), cyr = __fsub_rn(cyf, floorf(d.y));
+    add_corners(z, cell_frac(mf, r.x, r.z, d.z, cxr), cell_frac(mf, r.y, r.w, d.w, cyr), w);
 }
 } // namespace
 
@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
         const int count = dp.cell_cnt[in.list_off + cell];
         const int nv = (count + 3) >> 2;
         const int v0 = (int)(((int64_t)it.group * nv) / G), v1 = (int)(((int64_t)(it.group + 1) * nv) / G);
-        const float2* det = reinterpret_cast<const float2*>(dp.detUV) + in.det_off;
-        const float2* trig = dp.trig + in.trig_off;
+        const float4* det = dp.det + in.det_off;
+        const float4* rays = dp.rays + in.ray_off;
         const float* mb = dp.mbar + in.mbar_off;
         const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
         const uint32_t qmask = (1u << qb) - 1u, mmask = (1u << in.code_mbits) - 1u;
@@ -219,10 +219,10 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
             for (int u = 0; u < 4; ++u) {
                 const int k = (vb + u) * 4;
                 if (vb + u >= v1) break;
-                list_sample(c[u].x, qb, mbq, mmask, qmask, det, trig, mb, in.n_rp, in.delta, cxf, cyf, z);
-                if (k + 1 < count) list_sample(c[u].y, qb, mbq, mmask, qmask, det, trig, mb, in.n_rp, in.delta, cxf, cyf, z);
-                if (k + 2 < count) list_sample(c[u].z, qb, mbq, mmask, qmask, det, trig, mb, in.n_rp, in.delta, cxf, cyf, z);
-                if (k + 3 < count) list_sample(c[u].w, qb, mbq, mmask, qmask, det, trig, mb, in.n_rp, in.delta, cxf, cyf, z);
+                list_sample(c[u].x, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
+                if (k + 1 < count) list_sample(c[u].y, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
+                if (k + 2 < count) list_sample(c[u].z, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
+                if (k + 3 < count) list_sample(c[u].w, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
             }
         }
         dp.zbuf[in.z_off + (size_t)it.group * w * w + cell] = z;

@@ -7,16 +7,26 @@
 // so pixel (iy, ix) sits at (ix - c0, iy - c0) and cell (i0, j0) (the unit
 // square whose lower-left corner is pixel (i0, j0)) is
 // [i0 - c0, i0 - c0 + 1) x [j0 - c0, j0 - c0 + 1).  Centring halves the
-// magnitude of the coordinates and so halves their FP32 rounding error.
+// magnitude of the coordinates.
 //
 // A sample of the circular mean about detector j at radius index m and angle
-// index q is
-//     ubar = fma(rho_m, cos_q, U_j),   vbar = fma(rho_m, sin_q, V_j),
-// with rho_m = float(m) * delta, (cos_q, sin_q) and (U_j, V_j) read from the
-// plan's FP32 tables.  The forward gather and the adjoint gather evaluate
-// exactly this expression (explicit __fmaf_rn, no contraction freedom), so
-// both kernels see every sample in the same cell with the same bilinear
-// weights: the adjoint is the transpose of the forward matrix.
+// index q sits at (U_j + m dcos_q, V_j + m dsin_q), dcos_q = delta cos(2 pi q/K).
+// FP32 cannot hold that point to better than half an ulp of |ubar| (up to
+// N/2), which at N >= 384 alone costs ~1e-5 of relative error in A and A^T.
+// The kernels therefore work in split form:
+//   * detector: U = float(U_j), Ui = floor(U), Uf = float(U_j - Ui);
+//   * direction: dcos_q = hi + lo (two FP32 numbers, from FP64);
+//   * cell (relative to Ui):  cu = floor(fma(m, hi, Uf));
+//   * fraction in the cell:   a  = fma(m, hi, -cu) + fma(m, lo, Uf),
+// and the same for v.  m * hi is exact inside the FMA and the rounded
+// results are below 2 in magnitude, so a is within ~3 * 2^-25 of the exact
+// fraction at any N (the cell decision itself may differ from the exact one
+// only for samples within ~N * 2^-24 of a grid line, where both cells give
+// the same interpolated value to that order).  The forward gather and the
+// adjoint gather evaluate exactly these expressions (explicit __fmaf_rn /
+// __fadd_rn, no contraction freedom), so both kernels see every sample in
+// the same cell with the same bilinear weights: the adjoint is the transpose
+// of the forward matrix.
 #pragma once
 
 #include <cstddef>
@@ -34,7 +44,7 @@ constexpr int kCircQueueBase = 4; // work_counters[4 + 2 t], [5 + 2 t]: queue of
 // Per-instance descriptor (device resident, read by every kernel).
 struct InstDev {
     int32_t n, n_det, n_t, n_r;
-    int32_t K, c0, det_off, trig_off;
+    int32_t K, c0, det_off, pad1;
     float delta, inv_delta, dphi, inv_dphi;
     float inv_K, pad0;
     int32_t n_slots, nmb;          // forward partial slots; radius blocks per detector
@@ -44,7 +54,7 @@ struct InstDev {
     int64_t p_off;                 // float offset of P (n_t rows, pitch n_rp), then P^T (n_r rows, pitch n_tp)
     int64_t slotcnt_off;           // byte offset of the slot counts (n_det x nmb int32)
     int64_t z_off;                 // float4 offset of the adjoint cell sums (groups x (n+1)^2)
-    int64_t rtrig_off;             // float2 offset of (1/(cos_q delta), 1/(sin_q delta)), 2K entries
+    int64_t ray_off;               // entry offset of the instance's 2K rays and reciprocal rays
     int64_t arrive_off;            // int offset of the slot-arrival counters (n_det x nmb)
     int64_t list_off;              // adjoint list mode: offset of the (n+1)^2 + 1 cell offsets
     int32_t code_qbits, code_mbits; // adjoint list mode: code = j << (qb+mb) | m << qb | q
@@ -93,10 +103,9 @@ struct ImgTile {
 // Everything a kernel launch needs, by value (fits the 4 KB parameter space).
 struct DevPlan {
     const InstDev* inst;
-    const float* detU;             // U_j (centred pixel units), concatenated per instance
-    const float* detV;
-    const float2* trig;            // (cos, sin)(2 pi q / K), 2K entries per distinct K
-    const float2* rtrig;           // per instance: (1/(cos_q delta), 1/(sin_q delta)), 2K entries
+    const float4* det;             // (U, V, Uf, Vf) of each detector (split form), per instance
+    const float4* rays;            // (dcos hi, dsin hi, dcos lo, dsin lo) per q, 2K entries per instance
+    const float2* rtrig;           // (1/dcos hi, 1/dsin hi), 2K entries per instance
     const float* P;                // Abel matrices P then P^T, per distinct n_t
     const uint8_t* slotcnt;        // forward slots per (detector, radius block), int32
     const Unit* units;
@@ -106,7 +115,6 @@ struct DevPlan {
     const TimeTile* adj_tiles;
     const CellItem* cell_items;
     const ImgTile* img_tiles;
-    const float* detUV;            // (U_j, V_j) interleaved (float2), concatenated per instance
     const int64_t* cell_off;       // adjoint list mode: start of each cell's codes (multiple of 4)
     const int32_t* cell_cnt;       // adjoint list mode: number of codes of each cell
     const uint32_t* codes;         // adjoint list mode: packed (j, m, q) of every sample, by cell

@@ -228,20 +228,10 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         P.g_offsets[i + 1] = P.g_offsets[i] + (int64_t)geoms[i].n_det * geoms[i].n_t;
     }
 
-    // ---- distinct K (trig) and n_t (Abel matrices P, then P^T) ------------
-    std::map<int, int64_t> trig_off, p_off;
-    std::vector<float2> trig;
+    // ---- distinct n_t (Abel matrices P, then P^T) --------------------------
+    std::map<int, int64_t> p_off;
     std::vector<float> pmat;
     for (int i = 0; i < n_inst; ++i) {
-        const int K = geoms[i].n_angles;
-        if (!trig_off.count(K)) {
-            trig_off[K] = (int64_t)trig.size();
-            for (int q = 0; q < 2 * K; ++q) {
-                const int qq = q % K;
-                const double ph = kTwoPi * qq / K;
-                trig.push_back(make_float2((float)std::cos(ph), (float)std::sin(ph)));
-            }
-        }
         const int nt = geoms[i].n_t;
         if (!p_off.count(nt)) {
             // P (nt rows, pitch nrp) then P^T (nr rows, pitch ntp); padding is zero
@@ -262,7 +252,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     std::map<GeomKey, int> tmpl_index;
     std::vector<GeomTemplate> tmpls;
     std::vector<int> inst_tmpl(n_inst);
-    std::vector<float> detU, detV;
+    std::vector<float> detU, detV;     // FP32 detector coordinates (host geometry)
+    std::vector<float4> det4, rays;
     std::vector<float2> rtrig;
     std::vector<InstDev> inst(n_inst);
     int band_bytes = 0;
@@ -298,12 +289,15 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         d.f_off = P.f_offsets[i];
         d.g_off = P.g_offsets[i];
         d.p_off = p_off[g.n_t];
-        d.trig_off = (int32_t)trig_off[g.n_angles];
         d.det_off = (int32_t)detU.size();
         for (int j = 0; j < g.n_det; ++j) {
+            // split form: U (FP32), and the exact U minus floor(U) in FP32
             const double th = g.arc_start + (j + 0.5) * g.arc_span / g.n_det;
-            detU.push_back((float)(std::cos(th) * (n / 2.0) - 0.5));
-            detV.push_back((float)(std::sin(th) * (n / 2.0) - 0.5));
+            const double ue = std::cos(th) * (n / 2.0) - 0.5, ve = std::sin(th) * (n / 2.0) - 0.5;
+            const float uf = (float)ue, vf = (float)ve;
+            detU.push_back(uf);
+            detV.push_back(vf);
+            det4.push_back(make_float4(uf, vf, (float)(ue - std::floor((double)uf)), (float)(ve - std::floor((double)vf))));
         }
         // reciprocal ray slopes for the adjoint's slab test, from the FP32 table values
         {
@@ -312,16 +306,22 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             d.code_mbits = bits(d.n_r);
             P.code_bits_max = std::max(P.code_bits_max, d.code_qbits + d.code_mbits + bits(g.n_det));
         }
-        d.rtrig_off = (int64_t)rtrig.size();
+        // rays: delta (cos, sin)(2 pi q / K) as FP32 hi + lo pairs (2K entries so
+        // that angle windows may run past K), and 1/hi for the adjoint's slab test
+        d.ray_off = (int64_t)rays.size();
         {
-            const float2* tq = &trig[d.trig_off];
-            auto rcp = [&](float c) {
-                const double x = (double)c * (double)d.delta;
-                if (std::fabs(x) < 1e-30) return 1e30f;
-                const double r = 1.0 / x;
+            auto rcp = [](float x) {
+                if (std::fabs((double)x) < 1e-30) return 1e30f;
+                const double r = 1.0 / (double)x;
                 return (float)std::max(-1e30, std::min(1e30, r));
             };
-            for (int q = 0; q < 2 * g.n_angles; ++q) rtrig.push_back(make_float2(rcp(tq[q].x), rcp(tq[q].y)));
+            for (int q = 0; q < 2 * g.n_angles; ++q) {
+                const double ph = kTwoPi * (q % g.n_angles) / g.n_angles;
+                const double dc = delta * std::cos(ph), ds = delta * std::sin(ph);
+                const float ch = (float)dc, sh = (float)ds;
+                rays.push_back(make_float4(ch, sh, (float)(dc - (double)ch), (float)(ds - (double)sh)));
+                rtrig.push_back(make_float2(rcp(ch), rcp(sh)));
+            }
         }
 
         GeomKey key{n, g.n_det, g.n_t, g.n_angles, bf16 ? 1 : 0, ml, qpiece, rows_max, g.arc_start, g.arc_span,
@@ -603,12 +603,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         return o;
     };
     const size_t o_inst = reserve(sizeof(InstDev) * inst.size());
-    const size_t o_detU = reserve(sizeof(float) * detU.size());
-    const size_t o_detV = reserve(sizeof(float) * detV.size());
-    std::vector<float2> detUV(detU.size());
-    for (size_t k = 0; k < detU.size(); ++k) detUV[k] = make_float2(detU[k], detV[k]);
-    const size_t o_detUV = reserve(sizeof(float2) * detUV.size());
-    const size_t o_trig = reserve(sizeof(float2) * trig.size());
+    const size_t o_det = reserve(sizeof(float4) * det4.size());
+    const size_t o_rays = reserve(sizeof(float4) * rays.size());
     const size_t o_rtrig = reserve(sizeof(float2) * rtrig.size());
     const size_t o_P = reserve(sizeof(float) * pmat.size());
     const size_t o_slot = reserve(sizeof(int32_t) * slotcnt.size());
@@ -632,10 +628,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         if (bytes) std::memcpy(host.data() + o, src, bytes);
     };
     put(o_inst, inst.data(), sizeof(InstDev) * inst.size());
-    put(o_detU, detU.data(), sizeof(float) * detU.size());
-    put(o_detV, detV.data(), sizeof(float) * detV.size());
-    put(o_detUV, detUV.data(), sizeof(float2) * detUV.size());
-    put(o_trig, trig.data(), sizeof(float2) * trig.size());
+    put(o_det, det4.data(), sizeof(float4) * det4.size());
+    put(o_rays, rays.data(), sizeof(float4) * rays.size());
     put(o_rtrig, rtrig.data(), sizeof(float2) * rtrig.size());
     put(o_P, pmat.data(), sizeof(float) * pmat.size());
     put(o_slot, slotcnt.data(), sizeof(int32_t) * slotcnt.size());
@@ -673,10 +667,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     DevPlan& dp = P.dp;
     std::memset(&dp, 0, sizeof(dp));
     dp.inst = reinterpret_cast<const InstDev*>(base + o_inst);
-    dp.detU = reinterpret_cast<const float*>(base + o_detU);
-    dp.detV = reinterpret_cast<const float*>(base + o_detV);
-    dp.detUV = reinterpret_cast<const float*>(base + o_detUV);
-    dp.trig = reinterpret_cast<const float2*>(base + o_trig);
+    dp.det = reinterpret_cast<const float4*>(base + o_det);
+    dp.rays = reinterpret_cast<const float4*>(base + o_rays);
     dp.rtrig = reinterpret_cast<const float2*>(base + o_rtrig);
     dp.P = reinterpret_cast<const float*>(base + o_P);
     dp.slotcnt = reinterpret_cast<const uint8_t*>(base + o_slot);
