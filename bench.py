@@ -409,6 +409,8 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     plan.set_timing(True)
+    if args.profile:
+        torch.cuda.profiler.start()   # ncu --profile-from-start off: capture the timed steps only
     for i in range(n_steps):
         if not args.profile:
             flush.fill_(float(i))
@@ -416,6 +418,8 @@ def main():
         step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.stop()
     if world > 1:
         torch.distributed.barrier()
     plan.set_timing(False)

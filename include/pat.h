@@ -99,9 +99,11 @@ typedef struct {
     int32_t q_piece;     /* max angular nodes per work unit (multiple of 4); 0 = auto        */
     int32_t band_rows;   /* max image rows per shared-memory band; 0 = auto                  */
     int32_t adj_groups;  /* detector groups of the adjoint gather, 1..16; 0 = auto           */
-    int32_t adj_mode;    /* adjoint gather: 0 = auto, 1 = per-cell sample lists built at      */
-                         /*   creation (device memory ~4 B per sample), 2 = enumerate on      */
-                         /*   every call (no list memory)                                     */
+    int32_t adj_mode;    /* adjoint gather: 0 = auto (3 if it fits the list budget, else 1,   */
+                         /*   else 2), 1 = per-cell sample code lists built at creation       */
+                         /*   (device memory ~4 B per sample), 2 = enumerate on every call    */
+                         /*   (no list memory), 3 = per-cell fraction lists built at creation */
+                         /*   (~12 B per sample: Mbar index and the FP32 bilinear fractions)  */
     int32_t reserved[8];
 } pat_options_t;
 
@@ -118,7 +120,8 @@ typedef struct {
     int64_t device_bytes;    /* device memory held by the plan                            */
     int32_t m_lanes, q_piece, band_rows, adj_groups; /* tile shape in use              */
     int32_t bands_max;       /* largest number of bands of any instance                   */
-    int32_t adj_mode;        /* adjoint gather in use: 1 = sample lists, 2 = enumeration  */
+    int32_t adj_mode;        /* adjoint gather in use: 1 = code lists, 2 = enumeration,   */
+                             /*   3 = fraction lists                                      */
     int64_t list_bytes;      /* device memory of the adjoint sample lists                 */
     int32_t reserved[4];
 } pat_plan_info_t;

@@ -130,7 +130,7 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
     if (opt.q_piece < 4 || opt.q_piece % 4 != 0) return PAT_ERR_INVALID_ARG;
     if (opt.band_rows != 0 && (opt.band_rows < 3 || opt.band_rows > 8192)) return PAT_ERR_INVALID_ARG;
     if (opt.adj_groups < 0 || opt.adj_groups > 16) return PAT_ERR_INVALID_ARG;
-    if (opt.adj_mode < 0 || opt.adj_mode > 2) return PAT_ERR_INVALID_ARG;
+    if (opt.adj_mode < 0 || opt.adj_mode > 3) return PAT_ERR_INVALID_ARG;
     const bool bf16 = opt.image_dtype == PAT_BF16;
     for (int i = 0; i < n_instances; ++i)
         if (!valid_geometry(geoms[i], bf16)) return PAT_ERR_INVALID_ARG;

@@ -7,8 +7,9 @@
 //
 // Persistent CTAs.  The work is split into band tasks (an image band of one
 // instance and the units whose samples can fall in it).  CTA c works on band
-// tasks cta_seg[c] .. cta_seg[c+1]-1; for each it stages the band in shared
-// memory (TMA bulk copies, one per image row, completing on an mbarrier) and
+// tasks cta_seg[c] .. cta_seg[c+1]-1; for each it stages the band and the
+// instance's K ray directions in shared memory (TMA bulk copies, one per
+// image row and one for the rays, completing on an mbarrier) and
 // its warps take units, largest first, from the task's global queue, which
 // all CTAs assigned to the task share (the last one to finish re-arms it).
 // Lane l of a warp handles radius m0 + l % ML and angles
@@ -22,24 +23,22 @@ namespace patgpu {
 
 namespace {
 
-// One bilinear sample of the staged band; 0 for samples whose cell lies
-// outside the band (they belong to another band or to no pixel).  s points at
-// the detector's integer cell (Ui, Vi); cells and bounds are relative to it.
+// One bilinear sample of the staged band, branch free: a sample whose cell
+// lies outside the band (it belongs to another band or to no pixel) reads the
+// zero 2 x 2 block at offset 1 of the band's left padding instead.  Cells are
+// relative to the detector's integer part (Ui, Vi); `base` is the offset of
+// cell (Ui, Vi) in the band, and the relative cell (iu, iv) is inside the band
+// iff iu - ul <= uw and iv - vl <= vw (unsigned).
 template <typename T>
-__device__ __forceinline__ float sample(const T* __restrict__ s, int W, float mf, float4 r, float Uf, float Vf,
-                                        float ulo, float uhi, float vlo, float vhi)
+__device__ __forceinline__ float sample(const T* __restrict__ s, int W, int base, float mf, float4 r, float Uf,
+                                        float Vf, int ul, unsigned uw, int vl, unsigned vw)
 {
     const float fu = cell_rel(mf, r.x, Uf), fv = cell_rel(mf, r.y, Vf);
-    const bool ok = (fu >= ulo) & (fu <= uhi) & (fv >= vlo) & (fv <= vhi);
+    const int iu = __float2int_rz(fu), iv = __float2int_rz(fv);
+    const bool ok = ((unsigned)(iu - ul) <= uw) & ((unsigned)(iv - vl) <= vw);
+    const T* p = s + (ok ? iv * W + iu + base : 1);
     const float a = cell_frac(mf, r.x, r.z, Uf, fu), b = cell_frac(mf, r.y, r.w, Vf, fv);
-    const T* p = s + (__float2int_rz(fv) * W + __float2int_rz(fu));
-    float f00 = 0.f, f10 = 0.f, f01 = 0.f, f11 = 0.f;
-    if (ok) {
-        f00 = ld_img(p);
-        f10 = ld_img(p + 1);
-        f01 = ld_img(p + W);
-        f11 = ld_img(p + W + 1);
-    }
+    const float f00 = ld_img(p), f10 = ld_img(p + 1), f01 = ld_img(p + W), f11 = ld_img(p + W + 1);
     const float top = fmaf(a, f10 - f00, f00);
     const float bot = fmaf(a, f11 - f01, f01);
     return fmaf(b, bot - top, top);
@@ -53,6 +52,7 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     T* s = reinterpret_cast<T*>(smem_raw);
+    float4* rays_s = reinterpret_cast<float4*>(smem_raw + dp.fwd_rays_off);
     constexpr int QL = kWarp / ML;
     constexpr int CO = ImgTraits<T>::col_off;
     const int lane = threadIdx.x & 31;
@@ -79,20 +79,23 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
         if (threadIdx.x < 32) {
             const int r0 = max(sg.band_lo, 0), r1 = min(sg.band_hi, n - 1);
             const uint32_t row_bytes = (uint32_t)n * sizeof(T);
+            const uint32_t ray_bytes = (uint32_t)in.K * (uint32_t)sizeof(float4);
             if (lane == 0) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bar, r1 >= r0 ? (uint32_t)(r1 - r0 + 1) * row_bytes : 0u);
+                mbar_arrive_expect_tx(&bar, (r1 >= r0 ? (uint32_t)(r1 - r0 + 1) * row_bytes : 0u) + ray_bytes);
+                bulk_g2s(rays_s, dp.rays + in.ray_off, ray_bytes, &bar);
             }
             __syncwarp();
             for (int r = r0 + lane; r <= r1; r += 32)
                 bulk_g2s(s + (r - sg.band_lo) * W + CO, f + in.f_off + (size_t)r * n, row_bytes, &bar);
         }
-        // ---- zero borders: columns -1 and N.. (pad), rows outside the image
+        // ---- zero borders: columns 0 .. CO-1 and N+CO .. W-1 (padding), rows
+        // outside the image; columns 1, 2 of rows 0, 1 are the zero block
         const T zero = T(0.f);
         const int pad = W - (CO + n);
-        for (int i = threadIdx.x; i < rows * (pad + 1); i += blockDim.x) {
-            const int ri = i / (pad + 1), c = i - ri * (pad + 1);
-            s[ri * W + (c == 0 ? CO - 1 : CO + n + c - 1)] = zero;
+        for (int i = threadIdx.x; i < rows * (pad + CO); i += blockDim.x) {
+            const int ri = i / (pad + CO), c = i - ri * (pad + CO);
+            s[ri * W + (c < CO ? c : n + c)] = zero;
         }
         for (int ri = 0; ri < rows; ++ri) {
             const int r = sg.band_lo + ri;
@@ -107,12 +110,10 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
         parity ^= 1u;
 
         // ---- units: shared queue of every CTA working on this band task ----
-        // cell (i0c, j0c) in centred units lives at s[j0c * W + i0c + base]
-        const T* sb = s + ((in.c0 - sg.band_lo) * W + in.c0 + CO);
-        const float ulo = (float)(-1 - in.c0), uhi = (float)(n - 1 - in.c0);
-        const float vlo = (float)(sg.band_lo - in.c0), vhi = (float)(sg.band_hi - 1 - in.c0);
+        // centred cell (i0c, j0c) lives at s[(j0c + c0 - band_lo) * W + i0c + c0 + CO]
+        const int ulo = -1 - in.c0, vlo = sg.band_lo - in.c0;
+        const unsigned uw = (unsigned)n, vw = (unsigned)(sg.band_hi - 1 - sg.band_lo);
         const float4* det = dp.det + in.det_off;
-        const float4* rays = dp.rays + in.ray_off;
         const Unit* units = dp.units + sg.unit_begin;
         int32_t* queue = dp.work_counters + kCircQueueBase + 2 * sg.queue;
 
@@ -132,20 +133,20 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
             const int m = un.m0 + ml;
             const float mf = (float)m;
             const float4 d = __ldg(det + un.j);
-            const float Ui = floorf(d.x), Vi = floorf(d.y);
-            const T* sj = sb + (__float2int_rz(Vi) * W + __float2int_rz(Ui));
-            const float ul = ulo - Ui, uh = uhi - Ui, vl = vlo - Vi, vh = vhi - Vi;
-            const float4* tq = rays + un.q0 + ql;
+            const int Ui = __float2int_rz(floorf(d.x)), Vi = __float2int_rz(floorf(d.y));
+            const int base = (Vi + in.c0 - sg.band_lo) * W + Ui + in.c0 + CO;
+            const int ul = ulo - Ui, vl = vlo - Vi;
+            const float4* tq = rays_s + un.q0 + ql;   // units never wrap past K
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
             int i = ql;
             for (; i + 3 * QL < un.nq; i += 4 * QL, tq += 4 * QL) {
-                const float4 c0 = __ldg(tq), c1 = __ldg(tq + QL), c2 = __ldg(tq + 2 * QL), c3 = __ldg(tq + 3 * QL);
-                acc0 += sample(sj, W, mf, c0, d.z, d.w, ul, uh, vl, vh);
-                acc1 += sample(sj, W, mf, c1, d.z, d.w, ul, uh, vl, vh);
-                acc2 += sample(sj, W, mf, c2, d.z, d.w, ul, uh, vl, vh);
-                acc3 += sample(sj, W, mf, c3, d.z, d.w, ul, uh, vl, vh);
+                const float4 c0 = tq[0], c1 = tq[QL], c2 = tq[2 * QL], c3 = tq[3 * QL];
+                acc0 += sample(s, W, base, mf, c0, d.z, d.w, ul, uw, vl, vw);
+                acc1 += sample(s, W, base, mf, c1, d.z, d.w, ul, uw, vl, vw);
+                acc2 += sample(s, W, base, mf, c2, d.z, d.w, ul, uw, vl, vw);
+                acc3 += sample(s, W, base, mf, c3, d.z, d.w, ul, uw, vl, vw);
             }
-            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(sj, W, mf, __ldg(tq), d.z, d.w, ul, uh, vl, vh);
+            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(s, W, base, mf, *tq, d.z, d.w, ul, uw, vl, vw);
             float acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
             for (int o = ML; o < kWarp; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

@@ -14,11 +14,14 @@
 // that can land in it, and each candidate's cell is re-evaluated with exactly
 // the forward's split-form expression.  Hits come out in the order (j, q, m).
 //
-// Two ways to run this:
-//   list mode (default when the codes fit): at plan creation the enumeration
-//     runs twice (count, then fill) to store every cell's hits as packed
-//     (j, m, q) codes; each call is then a warp-per-cell gather over that
-//     list that recomputes the weights from the codes.
+// Three ways to run this:
+//   fraction lists (default when 12 B per sample fits the list budget): at
+//     plan creation the enumeration runs twice (count, then fill) to store
+//     every cell's hits as (Mbar index, a, b), a and b the exact FP32 values
+//     the forward computes; each call then streams the lists and gathers
+//     Mbar (one table load per sample, no coordinate arithmetic).
+//   code lists (4 B per sample): the hits as packed (j, m, q) codes; each
+//     call recomputes a and b from the codes with the forward's expressions.
 //   compute mode: the enumeration runs on every call (k_adj_cells), one warp
 //     per 8 x 4 patch of cells and detector group, partial Z per group.
 #include "device_common.cuh"
@@ -139,12 +142,15 @@ __global__ void __launch_bounds__(256, 5) k_adj_cells(DevPlan dp)
 }
 
 // ---------------------------------------------------------------------------
-// List building (plan creation): count, then fill, the hits of every cell of
-// instance `inst_idx`, all detectors, in enumeration order.  Thread = cell.
+// List building (plan creation): count (MODE 0), then fill, the hits of every
+// cell of instance `inst_idx`, all detectors, in enumeration order.  Thread =
+// cell.  MODE 1 writes packed (j, m, q) codes; MODE 2 writes fraction lists,
+// 48-byte vectors of four samples: four Mbar indices j * n_rp + m, four a,
+// four b (a cell's list starts on a vector: its offset is a multiple of 4).
 // ---------------------------------------------------------------------------
-template <int FILL>
+template <int MODE>
 __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int32_t* __restrict__ counts,
-                                                   const int64_t* __restrict__ offs, uint32_t* __restrict__ codes)
+                                                   const int64_t* __restrict__ offs, uint32_t* __restrict__ out)
 {
     const InstDev in = dp.inst[inst_idx];
     const int n = in.n, w = n + 1;
@@ -152,13 +158,19 @@ __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int
     if (idx >= w * w) return;
     const int cx = idx % w - 1, cy = idx / w - 1;
     const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
-    int64_t k = FILL ? offs[idx] : 0;
+    int64_t k = MODE ? offs[idx] : 0;
     const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
-    enumerate_cell(dp, in, cxf, cyf, 0, 1, [&](int j, int m, int q, float, float) {
-        if (FILL) codes[k] = ((uint32_t)j << mbq) | ((uint32_t)m << qb) | (uint32_t)q;
+    enumerate_cell(dp, in, cxf, cyf, 0, 1, [&](int j, int m, int q, float a, float b) {
+        if (MODE == 1) out[k] = ((uint32_t)j << mbq) | ((uint32_t)m << qb) | (uint32_t)q;
+        if (MODE == 2) {
+            uint32_t* v = out + (k >> 2) * 12 + (k & 3);
+            v[0] = (uint32_t)(j * in.n_rp + m);
+            v[4] = __float_as_uint(a);
+            v[8] = __float_as_uint(b);
+        }
         ++k;
     });
-    if (!FILL) counts[idx] = (int32_t)k;
+    if (!MODE) counts[idx] = (int32_t)k;
 }
 
 // ---------------------------------------------------------------------------
@@ -184,6 +196,7 @@ __device__ __forceinline__ void list_sample(const uint32_t code, int qb, int mbq
 }
 } // namespace
 
+template <bool FRAC>
 __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
 {
     const int lane = threadIdx.x & 31;
@@ -198,31 +211,62 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
         const int cx = it.x0 + (lane & (kPatchW - 1)), cy = it.y0 + lane / kPatchW;
         if (cx > n - 1 || cy > n - 1) continue;
         const int cell = (cy + 1) * w + (cx + 1);
-        const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
         const int64_t beg = dp.cell_off[in.list_off + cell];       // multiple of 4
         const int count = dp.cell_cnt[in.list_off + cell];
         const int nv = (count + 3) >> 2;
         const int v0 = (int)(((int64_t)it.group * nv) / G), v1 = (int)(((int64_t)(it.group + 1) * nv) / G);
-        const float4* det = dp.det + in.det_off;
-        const float4* rays = dp.rays + in.ray_off;
         const float* mb = dp.mbar + in.mbar_off;
-        const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
-        const uint32_t qmask = (1u << qb) - 1u, mmask = (1u << in.code_mbits) - 1u;
-        const uint4* c4 = reinterpret_cast<const uint4*>(dp.codes + beg);
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        // four 16-byte vectors in flight per lane, then their up to 16 samples
-        for (int vb = v0; vb < v1; vb += 4) {
-            uint4 c[4];
+        if constexpr (FRAC) {
+            // two 48-byte vectors (8 samples) in flight per lane
+            const uint4* L = reinterpret_cast<const uint4*>(dp.codes) + (beg >> 2) * 3;
+            for (int vb = v0; vb < v1; vb += 2) {
+                uint4 ci[2], ca[2], cb[2];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) c[u] = (vb + u < v1) ? __ldg(c4 + vb + u) : make_uint4(0u, 0u, 0u, 0u);
+                for (int u = 0; u < 2; ++u) {
+                    if (vb + u < v1) {
+                        const uint4* p = L + (size_t)(vb + u) * 3;
+                        ci[u] = __ldcs(p);
+                        ca[u] = __ldcs(p + 1);
+                        cb[u] = __ldcs(p + 2);
+                    } else {
+                        ci[u] = ca[u] = cb[u] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = (vb + u) * 4;
-                if (vb + u >= v1) break;
-                list_sample(c[u].x, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
-                if (k + 1 < count) list_sample(c[u].y, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
-                if (k + 2 < count) list_sample(c[u].z, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
-                if (k + 3 < count) list_sample(c[u].w, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
+                for (int u = 0; u < 2; ++u) {
+                    if (vb + u >= v1) break;
+                    const int k = (vb + u) * 4;
+                    add_corners(z, __uint_as_float(ca[u].x), __uint_as_float(cb[u].x), __ldg(mb + ci[u].x));
+                    if (k + 1 < count)
+                        add_corners(z, __uint_as_float(ca[u].y), __uint_as_float(cb[u].y), __ldg(mb + ci[u].y));
+                    if (k + 2 < count)
+                        add_corners(z, __uint_as_float(ca[u].z), __uint_as_float(cb[u].z), __ldg(mb + ci[u].z));
+                    if (k + 3 < count)
+                        add_corners(z, __uint_as_float(ca[u].w), __uint_as_float(cb[u].w), __ldg(mb + ci[u].w));
+                }
+            }
+        } else {
+            const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
+            const float4* det = dp.det + in.det_off;
+            const float4* rays = dp.rays + in.ray_off;
+            const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
+            const uint32_t qmask = (1u << qb) - 1u, mmask = (1u << in.code_mbits) - 1u;
+            const uint4* c4 = reinterpret_cast<const uint4*>(dp.codes + beg);
+            // four 16-byte vectors in flight per lane, then their up to 16 samples
+            for (int vb = v0; vb < v1; vb += 4) {
+                uint4 c[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) c[u] = (vb + u < v1) ? __ldg(c4 + vb + u) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = (vb + u) * 4;
+                    if (vb + u >= v1) break;
+                    list_sample(c[u].x, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
+                    if (k + 1 < count) list_sample(c[u].y, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
+                    if (k + 2 < count) list_sample(c[u].z, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
+                    if (k + 3 < count) list_sample(c[u].w, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
+                }
             }
         }
         dp.zbuf[in.z_off + (size_t)it.group * w * w + cell] = z;
@@ -263,10 +307,12 @@ int adj_cells_blocks_per_sm()
     return nb;
 }
 
-int adj_list_blocks_per_sm()
+int adj_list_blocks_per_sm(bool frac)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_list, 256, 0) != cudaSuccess) {
+    const void* fn = frac ? reinterpret_cast<const void*>(k_adj_list<true>)
+                          : reinterpret_cast<const void*>(k_adj_list<false>);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -274,20 +320,22 @@ int adj_list_blocks_per_sm()
 }
 
 cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* offs,
-                             uint32_t* codes, cudaStream_t st)
+                             uint32_t* out, bool frac, cudaStream_t st)
 {
     const int cells = (n + 1) * (n + 1);
     const int blocks = (cells + 255) / 256;
-    if (codes) k_adj_build<1><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, codes);
-    else k_adj_build<0><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, codes);
+    if (!out) k_adj_build<0><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, out);
+    else if (frac) k_adj_build<2><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, out);
+    else k_adj_build<1><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_cells(const DevPlan& dp, cudaStream_t st)
 {
-    if (dp.adj_mode == 1) {
+    if (dp.adj_mode == 1 || dp.adj_mode == 3) {
         if (dp.n_list_items == 0) return cudaSuccess;
-        k_adj_list<<<dp.cell_blocks, 256, 0, st>>>(dp);
+        if (dp.adj_mode == 3) k_adj_list<true><<<dp.cell_blocks, 256, 0, st>>>(dp);
+        else k_adj_list<false><<<dp.cell_blocks, 256, 0, st>>>(dp);
     } else {
         if (dp.n_cell_items == 0) return cudaSuccess;
         k_adj_cells<<<dp.cell_blocks, 256, 0, st>>>(dp);

@@ -117,7 +117,7 @@ struct DevPlan {
     const ImgTile* img_tiles;
     const int64_t* cell_off;       // adjoint list mode: start of each cell's codes (multiple of 4)
     const int32_t* cell_cnt;       // adjoint list mode: number of codes of each cell
-    const uint32_t* codes;         // adjoint list mode: packed (j, m, q) of every sample, by cell
+    const uint32_t* codes;         // adjoint lists: packed (j, m, q) codes, or 48-byte fraction vectors
     const CellItem* list_items;    // adjoint list mode: (patch, part) items, longest parts first
     float* mpart;                  // forward partial slots
     float* msum;                   // forward circular-mean sums M (same layout as Mbar)
@@ -131,9 +131,10 @@ struct DevPlan {
     int32_t n_inst;
     int32_t n_fwd_ctas, n_fwd_tiles, n_adj_tiles, n_cell_items, n_img_tiles, n_list_items;
     int32_t m_lanes, adj_groups;
-    int32_t adj_mode;              // 1 = list mode, 0 = compute mode
+    int32_t adj_mode;              // 3 = fraction lists, 1 = code lists, 0 = compute mode
     int32_t cell_blocks;           // CTAs of the adjoint cell kernel (8 warps each)
     int32_t fwd_smem_bytes;        // dynamic shared memory of the circular-mean kernel
+    int32_t fwd_rays_off;          // byte offset of the staged rays (after the largest band)
     int32_t abel_smem_bytes;       // dynamic shared memory of the Abel kernels
     int32_t bf16;                  // image storage is BF16
 };

@@ -258,12 +258,16 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     std::vector<InstDev> inst(n_inst);
     int band_bytes = 0;
     int bands_max = 0;
+    int K_max = 0;
+    for (int i = 0; i < n_inst; ++i) K_max = std::max(K_max, geoms[i].n_angles);
+    const int ray_bytes = K_max * (int)sizeof(float4);   // staged beside the band
 
     for (int i = 0; i < n_inst; ++i) {
         const pat_geometry_t& g = geoms[i];
         const int n = g.n;
         const int W = bf16 ? band_pitch_bf16(n) : band_pitch_f32(n);
-        int rows_max = opt.band_rows > 0 ? opt.band_rows : (P.band_budget_bytes / (W * esize));
+        int rows_max = opt.band_rows > 0 ? opt.band_rows
+                                         : (std::max(P.band_budget_bytes - ray_bytes, 16 * 1024) / (W * esize));
         rows_max = std::max(rows_max, 3);
         rows_max = std::min(rows_max, n + 2);
         const int nb = (n + 1 + (rows_max - 1) - 1) / (rows_max - 1);
@@ -381,11 +385,13 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                                                         : std::min(r.second * G, K);
                         int len = std::min(q1 - q0, K);
                         while (len > 0) {
-                            const int piece = std::min(len, qpiece);
+                            // pieces never wrap past K (the kernel indexes K staged rays)
+                            const int qs = q0 % K;
+                            const int piece = std::min(std::min(len, qpiece), K - qs);
                             Unit u{};
                             u.j = j;
                             u.m0 = m0;
-                            u.q0 = q0 % K;
+                            u.q0 = qs;
                             u.nq = piece;
                             per[b][j].push_back(u);
                             q0 += piece;
@@ -417,7 +423,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     // Band tasks: (instance, band) with the band's units, largest first.  Each
     // task gets CTAs in proportion to its cost (at least one); the CTAs of a
     // task share its unit queue.  Participants are placed on CTAs by LPT.
-    const int smem_bytes = band_bytes;
+    const int smem_bytes = band_bytes + ray_bytes;
     if (smem_bytes > P.max_smem_optin) return PAT_ERR_UNSUPPORTED;
     P.fwd_smem = smem_bytes;
     const int bps = circmean_blocks_per_sm(ml, bf16, smem_bytes);
@@ -504,10 +510,19 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     // the forward's evaluated-sample upper bound); its groups split each list
     int64_t slot_samples_all = 0;
     for (int i = 0; i < n_inst; ++i) slot_samples_all += tmpls[inst_tmpl[i]].slot_samples;
-    const bool list_fits = P.code_bits_max <= 32;
-    if (opt.adj_mode == 1 && !list_fits) return PAT_ERR_UNSUPPORTED;
-    const bool use_lists = opt.adj_mode == 1 || (opt.adj_mode == 0 && list_fits &&
-                                                 (double)slot_samples_all * 4.0 <= (double)P.list_budget_bytes);
+    // fraction lists (12 B per sample) when they fit the budget, else packed
+    // codes (4 B per sample, when the code bits fit), else enumeration
+    const bool codes_fit = P.code_bits_max <= 32;
+    if (opt.adj_mode == 1 && !codes_fit) return PAT_ERR_UNSUPPORTED;
+    int list_mode = opt.adj_mode;
+    if (list_mode == 0) {
+        const double budget = (double)P.list_budget_bytes;
+        list_mode = (double)slot_samples_all * 12.0 <= budget                ? 3
+                    : codes_fit && (double)slot_samples_all * 4.0 <= budget ? 1
+                                                                            : 2;
+    }
+    const bool use_lists = list_mode == 1 || list_mode == 3;
+    const bool frac_lists = list_mode == 3;
     int AG = opt.adj_groups;
     if (AG == 0) AG = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * resident_warps + patches - 1) / patches));
     // Items with an estimate of their cost (candidate rays per detector, from
@@ -534,7 +549,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     std::stable_sort(wit.begin(), wit.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
     int LG = 1;
     if (use_lists) {
-        const int lbps = adj_list_blocks_per_sm();
+        const int lbps = adj_list_blocks_per_sm(frac_lists);
         if (lbps < 1) return PAT_ERR_UNSUPPORTED;
         const int64_t lres = (int64_t)lbps * P.num_sms * 8;
         LG = opt.adj_groups > 0 ? opt.adj_groups
@@ -700,6 +715,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.adj_groups = AG;
     dp.cell_blocks = cell_blocks;
     dp.fwd_smem_bytes = smem_bytes;
+    dp.fwd_rays_off = band_bytes;
     dp.abel_smem_bytes = kAbelChunk * kWarp * (int)sizeof(float) + kAbelChunk * (int)sizeof(float4);
     dp.bf16 = bf16 ? 1 : 0;
 
@@ -738,7 +754,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
             const int i = rep[t];
             const int cells = (inst[i].n + 1) * (inst[i].n + 1);
-            if (launch_adj_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, st) != cudaSuccess) s = PAT_ERR_CUDA;
+            if (launch_adj_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, false, st) != cudaSuccess)
+                s = PAT_ERR_CUDA;
             counts[t].resize(cells);
             if (s == PAT_OK && cudaMemcpyAsync(counts[t].data(), d_counts, sizeof(int32_t) * cells,
                                                cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -774,7 +791,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         const size_t b_offs = sizeof(int64_t) * offs_all.size();
         const size_t b_cnt = sizeof(int32_t) * cnt_all.size();
         const size_t b_items = sizeof(CellItem) * li.size();
-        const size_t b_codes = sizeof(uint32_t) * std::max<int64_t>(codes_total, 4);
+        const size_t b_codes = (frac_lists ? 12 : 4) * (size_t)std::max<int64_t>(codes_total, 4);
         const size_t o_cnt_l = align(b_offs), o_items_l = align(o_cnt_l + b_cnt), o_codes_l = align(o_items_l + b_items);
         list_bytes = (int64_t)(o_codes_l + b_codes);
         if (cudaMalloc(&P.d_lists, list_bytes) != cudaSuccess) {
@@ -802,13 +819,13 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (size_t t = 0; t < tmpls.size(); ++t) {
             const int i = rep[t];
             if (launch_adj_build(dp, i, inst[i].n, nullptr, dp.cell_off + tmpl_list_off[t],
-                                 reinterpret_cast<uint32_t*>(lb + o_codes_l), st) != cudaSuccess)
+                                 reinterpret_cast<uint32_t*>(lb + o_codes_l), frac_lists, st) != cudaSuccess)
                 return PAT_ERR_CUDA;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
         dp.n_list_items = (int)li.size();
-        dp.adj_mode = 1;
-        const int lbps = adj_list_blocks_per_sm();
+        dp.adj_mode = frac_lists ? 3 : 1;
+        const int lbps = adj_list_blocks_per_sm(frac_lists);
         dp.cell_blocks = (int)std::max<int64_t>(
             1, std::min<int64_t>((int64_t)lbps * P.num_sms, ((int64_t)li.size() + 7) / 8));
         dp.adj_groups = LG;
@@ -832,7 +849,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     for (auto& T : tmpls)
         for (auto& b : T.bands) I.band_rows = std::max(I.band_rows, b.hi - b.lo + 1);
     I.adj_groups = dp.adj_groups;
-    I.adj_mode = dp.adj_mode == 1 ? 1 : 2;
+    I.adj_mode = dp.adj_mode == 0 ? 2 : dp.adj_mode;
     I.list_bytes = list_bytes;
     I.device_bytes += list_bytes;
     I.bands_max = bands_max;

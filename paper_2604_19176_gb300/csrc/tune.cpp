@@ -128,7 +128,9 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
     // ---- forward candidates ---------------------------------------------
     const int W = bf16 ? band_pitch_bf16(n_max) : band_pitch_f32(n_max);
     const int esize = bf16 ? 2 : 4;
-    const int max_rows = (227 * 1024) / (W * esize);
+    int K_max = 0;
+    for (int i = 0; i < n_inst; ++i) K_max = std::max(K_max, geoms[i].n_angles);
+    const int max_rows = (227 * 1024 - K_max * 16) / (W * esize);
     std::vector<int> rows_cands = {0};
     for (int nb : {1, 2, 4, 6}) {
         const int rows = (n_max + 1 + nb - 1) / nb + 1;
@@ -166,8 +168,9 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
     // ---- adjoint candidates (with the best forward shape) ------------------
     best_ms = 1e30f;
     pat_options_t fwd_opt = best_opt;
-    std::vector<std::pair<int, int>> adj_cands = {{opt.adj_mode, 0}};
-    for (int gcount : {1, 2, 4, 8}) adj_cands.push_back({opt.adj_mode, gcount});
+    std::vector<std::pair<int, int>> adj_cands;
+    for (int mode : opt.adj_mode == 0 ? std::vector<int>{0, 1} : std::vector<int>{opt.adj_mode})
+        for (int gcount : {0, 1, 2, 4, 8}) adj_cands.push_back({mode, gcount});
     for (auto& ac : adj_cands) {
         pat_options_t o = fwd_opt;
         o.adj_mode = ac.first;

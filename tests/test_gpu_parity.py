@@ -79,7 +79,7 @@ def test_forward_adjoint_vessel256_full_size(cuda_dev):
 @pytest.mark.parametrize("kw", [dict(m_lanes=16), dict(m_lanes=8), dict(q_piece=4), dict(band_rows=5),
                                 dict(band_rows=17, m_lanes=8, q_piece=12), dict(adj_groups=1, adj_mode=2), dict(adj_groups=3, adj_mode=2),
                                 dict(adj_groups=16, adj_mode=2), dict(adj_mode=1), dict(adj_mode=1, adj_groups=3),
-                                dict(tune=1)])
+                                dict(adj_mode=3), dict(adj_mode=3, adj_groups=5), dict(tune=1)])
 def test_tile_shapes_agree_with_oracle(cuda_dev, kw):
     g = Geometry(48, 24, 0.4, 1.3 * math.pi, 80, 2.0, 70)
     f = f32(inputs.gaussian_phantom(48, 5, seed=3) + 0.1 * inputs.random_image(48, seed=4))
@@ -316,3 +316,17 @@ def test_large_radius_positions_n384(cuda_dev):
     d = f32(inputs.random_data(48, 512, seed=92))
     assert rel(run_fwd(plan, f, cuda_dev), O.forward(og(g), f)) <= TOL
     assert rel(run_adj(plan, d, cuda_dev), O.adjoint(og(g), d)) <= TOL
+
+
+def test_code_and_fraction_lists_agree_bitwise(cuda_dev):
+    """Fraction lists store the a, b that code lists recompute, in the same
+    order: with the same list split the two adjoints are bitwise equal."""
+    g = Geometry(96, 40, 0.3, 1.5 * math.pi, 160, 2.0, 192)
+    d = torch.tensor(inputs.random_data(40, 160, seed=61), dtype=torch.float32, device=cuda_dev)
+    outs = []
+    for mode in (1, 3):
+        plan = PatPlan(g, device=cuda_dev, adj_mode=mode, adj_groups=3)
+        assert plan.info()["adj_mode"] == mode
+        outs.append(plan.adjoint(d).clone())
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1])
