@@ -144,13 +144,16 @@ __global__ void __launch_bounds__(256, 5) k_adj_cells(DevPlan dp)
 // ---------------------------------------------------------------------------
 // List building (plan creation): count (MODE 0), then fill, the hits of every
 // cell of instance `inst_idx`, all detectors, in enumeration order.  Thread =
-// cell.  MODE 1 writes packed (j, m, q) codes; MODE 2 writes fraction lists,
-// 48-byte vectors of four samples: four Mbar indices j * n_rp + m, four a,
-// four b (a cell's list starts on a vector: its offset is a multiple of 4).
+// cell.  A cell's hits form nv = ceil(count / 4) vectors of four, split into
+// G contiguous parts; the 32 cells of an 8 x 4 patch store their part g
+// interleaved in one block, vector k of lane l at 16-byte slot
+// base(patch, g) + (k * S + s) * 32 + l, so that a warp's loads are
+// contiguous.  MODE 1: S = 1, packed (j, m, q) codes.  MODE 2: S = 3,
+// slots s = 0, 1, 2 hold four Mbar indices j * n_rp + m, four a, four b.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int32_t* __restrict__ counts,
-                                                   const int64_t* __restrict__ offs, uint32_t* __restrict__ out)
+                                                   const int64_t* __restrict__ pbase, uint32_t* __restrict__ out)
 {
     const InstDev in = dp.inst[inst_idx];
     const int n = in.n, w = n + 1;
@@ -158,27 +161,49 @@ __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int
     if (idx >= w * w) return;
     const int cx = idx % w - 1, cy = idx / w - 1;
     const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
-    int64_t k = MODE ? offs[idx] : 0;
     const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
+    const int G = dp.adj_groups;
+    constexpr int S = MODE == 2 ? 3 : 1;
+    int nv = 0, lane = 0, cnt = 0;
+    const int64_t* pb = nullptr;
+    if (MODE) {
+        cnt = counts[idx];
+        nv = (cnt + 3) >> 2;
+        lane = ((cy + 1) % kPatchH) * kPatchW + (cx + 1) % kPatchW;
+        pb = pbase + ((int64_t)((cy + 1) / kPatchH) * in.patches_x + (cx + 1) / kPatchW) * G;
+    }
+    int g = 0, v0 = 0, v1 = MODE ? nv / G : 0;   // part g holds vectors [v0, v1)
+    int k = 0;
     enumerate_cell(dp, in, cxf, cyf, 0, 1, [&](int j, int m, int q, float a, float b) {
-        if (MODE == 1) out[k] = ((uint32_t)j << mbq) | ((uint32_t)m << qb) | (uint32_t)q;
-        if (MODE == 2) {
-            uint32_t* v = out + (k >> 2) * 12 + (k & 3);
-            v[0] = (uint32_t)(j * in.n_rp + m);
-            v[4] = __float_as_uint(a);
-            v[8] = __float_as_uint(b);
+        if (MODE && k < cnt) {   // (the fill sees exactly the counted hits; never write past them)
+            const int v = k >> 2;
+            while (v >= v1) {
+                ++g;
+                v0 = v1;
+                v1 = (int)(((int64_t)(g + 1) * nv) / G);
+            }
+            const int64_t slot = pb[g] + (int64_t)(v - v0) * S * kWarp + lane;
+            uint32_t* o = out + slot * 4 + (k & 3);
+            if (MODE == 1) {
+                o[0] = ((uint32_t)j << mbq) | ((uint32_t)m << qb) | (uint32_t)q;
+            } else {
+                o[0] = (uint32_t)(j * in.n_rp + m);
+                o[kWarp * 4] = __float_as_uint(a);
+                o[2 * kWarp * 4] = __float_as_uint(b);
+            }
         }
         ++k;
     });
-    if (!MODE) counts[idx] = (int32_t)k;
+    if (!MODE) counts[idx] = k;
 }
 
 // ---------------------------------------------------------------------------
 // List mode: thread = (cell, part of its list).  A warp owns an 8 x 4 patch
-// of cells and one of G contiguous parts of every cell's list (lists are
-// stored 16-byte aligned); each lane streams its part four codes at a time,
-// recomputes each sample exactly as the forward does and accumulates its
-// cell's corner sums in order.  Partial sums per part go to Z[part].
+// of cells and one of G contiguous parts of every cell's list, stored
+// interleaved (see k_adj_build); each lane streams its part, takes every
+// sample's a and b (stored, or recomputed from the code exactly as the
+// forward computes them) and accumulates its cell's corner sums in order.
+// Partial sums per part go to Z[part].
 // ---------------------------------------------------------------------------
 namespace {
 __device__ __forceinline__ void list_sample(const uint32_t code, int qb, int mbq, uint32_t mmask, uint32_t qmask,
@@ -211,32 +236,34 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
         const int cx = it.x0 + (lane & (kPatchW - 1)), cy = it.y0 + lane / kPatchW;
         if (cx > n - 1 || cy > n - 1) continue;
         const int cell = (cy + 1) * w + (cx + 1);
-        const int64_t beg = dp.cell_off[in.list_off + cell];       // multiple of 4
         const int count = dp.cell_cnt[in.list_off + cell];
         const int nv = (count + 3) >> 2;
         const int v0 = (int)(((int64_t)it.group * nv) / G), v1 = (int)(((int64_t)(it.group + 1) * nv) / G);
+        const int nk = v1 - v0;
+        const int64_t pbi = in.pbase_off + ((int64_t)((it.y0 + 1) / kPatchH) * in.patches_x + (it.x0 + 1) / kPatchW) * G +
+                            it.group;
+        const uint4* L = reinterpret_cast<const uint4*>(dp.codes) + dp.list_base[pbi] + lane;
         const float* mb = dp.mbar + in.mbar_off;
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (FRAC) {
-            // two 48-byte vectors (8 samples) in flight per lane
-            const uint4* L = reinterpret_cast<const uint4*>(dp.codes) + (beg >> 2) * 3;
-            for (int vb = v0; vb < v1; vb += 2) {
+            // two vectors (8 samples) in flight per lane
+            for (int kb = 0; kb < nk; kb += 2) {
                 uint4 ci[2], ca[2], cb[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    if (vb + u < v1) {
-                        const uint4* p = L + (size_t)(vb + u) * 3;
+                    if (kb + u < nk) {
+                        const uint4* p = L + (size_t)(kb + u) * 3 * kWarp;
                         ci[u] = __ldcs(p);
-                        ca[u] = __ldcs(p + 1);
-                        cb[u] = __ldcs(p + 2);
+                        ca[u] = __ldcs(p + kWarp);
+                        cb[u] = __ldcs(p + 2 * kWarp);
                     } else {
                         ci[u] = ca[u] = cb[u] = make_uint4(0u, 0u, 0u, 0u);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    if (vb + u >= v1) break;
-                    const int k = (vb + u) * 4;
+                    if (kb + u >= nk) break;
+                    const int k = (v0 + kb + u) * 4;
                     add_corners(z, __uint_as_float(ca[u].x), __uint_as_float(cb[u].x), __ldg(mb + ci[u].x));
                     if (k + 1 < count)
                         add_corners(z, __uint_as_float(ca[u].y), __uint_as_float(cb[u].y), __ldg(mb + ci[u].y));
@@ -252,16 +279,16 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
             const float4* rays = dp.rays + in.ray_off;
             const int qb = in.code_qbits, mbq = in.code_qbits + in.code_mbits;
             const uint32_t qmask = (1u << qb) - 1u, mmask = (1u << in.code_mbits) - 1u;
-            const uint4* c4 = reinterpret_cast<const uint4*>(dp.codes + beg);
-            // four 16-byte vectors in flight per lane, then their up to 16 samples
-            for (int vb = v0; vb < v1; vb += 4) {
+            // four vectors in flight per lane, then their up to 16 samples
+            for (int kb = 0; kb < nk; kb += 4) {
                 uint4 c[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) c[u] = (vb + u < v1) ? __ldg(c4 + vb + u) : make_uint4(0u, 0u, 0u, 0u);
+                for (int u = 0; u < 4; ++u)
+                    c[u] = (kb + u < nk) ? __ldcs(L + (size_t)(kb + u) * kWarp) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int k = (vb + u) * 4;
-                    if (vb + u >= v1) break;
+                    if (kb + u >= nk) break;
+                    const int k = (v0 + kb + u) * 4;
                     list_sample(c[u].x, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
                     if (k + 1 < count) list_sample(c[u].y, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
                     if (k + 2 < count) list_sample(c[u].z, qb, mbq, mmask, qmask, det, rays, mb, in.n_rp, cxf, cyf, z);
@@ -319,14 +346,14 @@ int adj_list_blocks_per_sm(bool frac)
     return nb;
 }
 
-cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* offs,
+cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
                              uint32_t* out, bool frac, cudaStream_t st)
 {
     const int cells = (n + 1) * (n + 1);
     const int blocks = (cells + 255) / 256;
-    if (!out) k_adj_build<0><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, out);
-    else if (frac) k_adj_build<2><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, out);
-    else k_adj_build<1><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, offs, out);
+    if (!out) k_adj_build<0><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
+    else if (frac) k_adj_build<2><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
+    else k_adj_build<1><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
     return cudaGetLastError();
 }
 

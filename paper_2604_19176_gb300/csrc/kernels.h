@@ -33,11 +33,12 @@ int circmean_blocks_per_sm(int m_lanes, bool bf16, int smem_bytes);
 int adj_cells_blocks_per_sm();
 int adj_list_blocks_per_sm(bool frac);
 
-// Adjoint list building at plan creation: counts (out == nullptr) or fills
-// (out != nullptr, offs = exclusive prefix sums of the counts, rounded up to
-// multiples of 4) the sample lists of every cell of instance inst_idx, as
-// packed codes (4 B per sample) or fraction lists (frac: 12 B per sample).
-cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* offs,
+// Adjoint list building at plan creation: counts the hits of every cell of
+// instance inst_idx into `counts` (out == nullptr), or, given those counts
+// and the instance's (patch, part) block bases `pbase` (16-byte units), fills
+// the interleaved lists as packed codes (4 B per sample) or fraction lists
+// (frac: 12 B per sample).
+cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
                              uint32_t* out, bool frac, cudaStream_t st);
 
 } // namespace patgpu

@@ -56,10 +56,12 @@ struct InstDev {
     int64_t z_off;                 // float4 offset of the adjoint cell sums (groups x (n+1)^2)
     int64_t ray_off;               // entry offset of the instance's 2K rays and reciprocal rays
     int64_t arrive_off;            // int offset of the slot-arrival counters (n_det x nmb)
-    int64_t list_off;              // adjoint list mode: offset of the (n+1)^2 + 1 cell offsets
+    int64_t list_off;              // adjoint lists: offset of the instance's (n+1)^2 cell counts
     int32_t code_qbits, code_mbits; // adjoint list mode: code = j << (qb+mb) | m << qb | q
     int32_t n_rp;                  // row pitch (multiple of 32) of M, Mbar and P
     int32_t n_tp;                  // row pitch (multiple of 32) of P^T
+    int32_t patches_x;             // 8 x 4 cell patches per row of patches: ceil((n+1)/8)
+    int64_t pbase_off;             // adjoint lists: offset of the instance's (patch, part) list bases
 };
 
 // Circular-mean work unit: radii [m0, m0 + m_lanes) of detector j, angles
@@ -115,8 +117,8 @@ struct DevPlan {
     const TimeTile* adj_tiles;
     const CellItem* cell_items;
     const ImgTile* img_tiles;
-    const int64_t* cell_off;       // adjoint list mode: start of each cell's codes (multiple of 4)
-    const int32_t* cell_cnt;       // adjoint list mode: number of codes of each cell
+    const int64_t* list_base;      // adjoint lists: first 16-byte vector of each (patch, part) block
+    const int32_t* cell_cnt;       // adjoint lists: number of hits of each cell
     const uint32_t* codes;         // adjoint lists: packed (j, m, q) codes, or 48-byte fraction vectors
     const CellItem* list_items;    // adjoint list mode: (patch, part) items, longest parts first
     float* mpart;                  // forward partial slots

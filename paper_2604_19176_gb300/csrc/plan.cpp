@@ -730,9 +730,14 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
 
     // ---- adjoint sample lists (list mode) --------------------------------------
-    // Each cell's codes are stored 16-byte aligned (offsets are multiples of 4).
+    // Hits are counted per cell, then stored per (8 x 4 patch, part): the 32
+    // cells' parts interleaved vector by vector, each block as long as the
+    // patch's longest part (see k_adj_build).
     int64_t list_bytes = 0;
     if (use_lists) {
+        const int S = frac_lists ? 3 : 1;     // 16-byte slots per vector of four samples
+        const int G = LG;
+        dp.adj_groups = G;                    // the fill kernel splits lists into G parts
         // count the hits of every cell, per geometry template (first instance)
         std::vector<int> rep(tmpls.size(), -1);
         for (int i = 0; i < n_inst; ++i)
@@ -746,10 +751,6 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             cudaGetLastError();
             return PAT_ERR_OOM;
         }
-        std::vector<int64_t> offs_all;
-        std::vector<int32_t> cnt_all;
-        std::vector<int64_t> tmpl_list_off(tmpls.size());
-        int64_t codes_total = 0;
         pat_status_t s = PAT_OK;
         for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
             const int i = rep[t];
@@ -761,38 +762,60 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                                                cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 s = PAT_ERR_CUDA;
             if (s == PAT_OK && cudaStreamSynchronize(st) != cudaSuccess) s = PAT_ERR_CUDA;
-            tmpl_list_off[t] = (int64_t)offs_all.size();
-            for (int c = 0; c < cells; ++c) {
-                offs_all.push_back(codes_total);
-                cnt_all.push_back(counts[t][c]);
-                codes_total += (counts[t][c] + 3) & ~3;
-            }
         }
         cudaFree(d_counts);
         if (s != PAT_OK) return s;
-        if (codes_total >= ((int64_t)1 << 40)) return PAT_ERR_UNSUPPORTED;
-        // list-mode work items: (patch, part), by the longest part in the patch
+        // block bases per (template, patch, part) and the longest part of each
+        std::vector<int32_t> cnt_all;
+        std::vector<int64_t> pbase_all;
+        std::vector<int64_t> tmpl_cnt_off(tmpls.size()), tmpl_pbase_off(tmpls.size());
+        std::vector<std::vector<int32_t>> part_len(tmpls.size());
+        int64_t slots_total = 0;   // 16-byte slots
+        for (size_t t = 0; t < tmpls.size(); ++t) {
+            const int n = inst[rep[t]].n, w = n + 1;
+            const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
+            tmpl_cnt_off[t] = (int64_t)cnt_all.size();
+            cnt_all.insert(cnt_all.end(), counts[t].begin(), counts[t].end());
+            tmpl_pbase_off[t] = (int64_t)pbase_all.size();
+            part_len[t].assign((size_t)pw * ph * G, 0);
+            for (int py = 0; py < ph; ++py)
+                for (int px = 0; px < pw; ++px)
+                    for (int g = 0; g < G; ++g) {
+                        int V = 0;
+                        for (int dy = 0; dy < kPatchH; ++dy)
+                            for (int dx = 0; dx < kPatchW; ++dx) {
+                                const int cxa = px * kPatchW + dx, cya = py * kPatchH + dy;  // cell + 1
+                                if (cxa >= w || cya >= w) continue;
+                                const int nv = (counts[t][(size_t)cya * w + cxa] + 3) >> 2;
+                                const int v0 = (int)(((int64_t)g * nv) / G), v1 = (int)(((int64_t)(g + 1) * nv) / G);
+                                V = std::max(V, v1 - v0);
+                            }
+                        part_len[t][((size_t)py * pw + px) * G + g] = V;
+                        pbase_all.push_back(slots_total);
+                        slots_total += (int64_t)V * S * kWarp;
+                    }
+            for (int i = 0; i < n_inst; ++i)
+                if (inst_tmpl[i] == (int)t) inst[i].patches_x = pw;
+        }
+        // list-mode work items: (patch, part), longest part first
         std::vector<std::pair<int32_t, CellItem>> li;
         for (int i = 0; i < n_inst; ++i) {
-            const auto& cn = counts[inst_tmpl[i]];
+            const int t = inst_tmpl[i];
             const int n = inst[i].n, w = n + 1;
-            for (int y0 = -1; y0 <= n - 1; y0 += kPatchH)
-                for (int x0 = -1; x0 <= n - 1; x0 += kPatchW) {
-                    int32_t mx = 0;
-                    for (int dy = 0; dy < kPatchH; ++dy)
-                        for (int dx = 0; dx < kPatchW; ++dx) {
-                            const int cx = x0 + dx, cy = y0 + dy;
-                            if (cx <= n - 1 && cy <= n - 1) mx = std::max(mx, cn[(size_t)(cy + 1) * w + cx + 1]);
-                        }
-                    for (int gg = 0; gg < LG; ++gg) li.push_back({mx, CellItem{i, x0, y0, gg}});
-                }
+            const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
+            for (int py = 0; py < ph; ++py)
+                for (int px = 0; px < pw; ++px)
+                    for (int g = 0; g < G; ++g) {
+                        const int32_t V = part_len[t][((size_t)py * pw + px) * G + g];
+                        if (V > 0) li.push_back({V, CellItem{i, px * kPatchW - 1, py * kPatchH - 1, g}});
+                    }
         }
         std::stable_sort(li.begin(), li.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-        const size_t b_offs = sizeof(int64_t) * offs_all.size();
+        const size_t b_pbase = sizeof(int64_t) * std::max<size_t>(pbase_all.size(), 1);
         const size_t b_cnt = sizeof(int32_t) * cnt_all.size();
-        const size_t b_items = sizeof(CellItem) * li.size();
-        const size_t b_codes = (frac_lists ? 12 : 4) * (size_t)std::max<int64_t>(codes_total, 4);
-        const size_t o_cnt_l = align(b_offs), o_items_l = align(o_cnt_l + b_cnt), o_codes_l = align(o_items_l + b_items);
+        const size_t b_items = sizeof(CellItem) * std::max<size_t>(li.size(), 1);
+        const size_t b_codes = 16 * (size_t)std::max<int64_t>(slots_total, 1);
+        const size_t o_cnt_l = align(b_pbase), o_items_l = align(o_cnt_l + b_cnt), o_codes_l = align(o_items_l + b_items);
         list_bytes = (int64_t)(o_codes_l + b_codes);
         if (cudaMalloc(&P.d_lists, list_bytes) != cudaSuccess) {
             P.d_lists = nullptr;
@@ -802,24 +825,30 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         unsigned char* lb = static_cast<unsigned char*>(P.d_lists);
         std::vector<CellItem> items(li.size());
         for (size_t k = 0; k < li.size(); ++k) items[k] = li[k].second;
-        if (cudaMemcpyAsync(lb, offs_all.data(), b_offs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        if (cudaMemcpyAsync(lb, pbase_all.data(), sizeof(int64_t) * pbase_all.size(), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
             cudaMemcpyAsync(lb + o_cnt_l, cnt_all.data(), b_cnt, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(lb + o_items_l, items.data(), b_items, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(lb + o_items_l, items.data(), sizeof(CellItem) * items.size(), cudaMemcpyHostToDevice,
+                            st) != cudaSuccess ||
             cudaMemsetAsync(lb + o_codes_l, 0, b_codes, st) != cudaSuccess)
             return PAT_ERR_CUDA;
-        dp.cell_off = reinterpret_cast<const int64_t*>(lb);
+        dp.list_base = reinterpret_cast<const int64_t*>(lb);
         dp.cell_cnt = reinterpret_cast<const int32_t*>(lb + o_cnt_l);
         dp.list_items = reinterpret_cast<const CellItem*>(lb + o_items_l);
         dp.codes = reinterpret_cast<const uint32_t*>(lb + o_codes_l);
-        for (int i = 0; i < n_inst; ++i) inst[i].list_off = tmpl_list_off[inst_tmpl[i]];
+        for (int i = 0; i < n_inst; ++i) {
+            inst[i].list_off = tmpl_cnt_off[inst_tmpl[i]];
+            inst[i].pbase_off = tmpl_pbase_off[inst_tmpl[i]];
+        }
         if (cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(InstDev) * inst.size(), cudaMemcpyHostToDevice, st) !=
             cudaSuccess)
             return PAT_ERR_CUDA;
         // fill the lists (same enumeration, same order)
         for (size_t t = 0; t < tmpls.size(); ++t) {
             const int i = rep[t];
-            if (launch_adj_build(dp, i, inst[i].n, nullptr, dp.cell_off + tmpl_list_off[t],
-                                 reinterpret_cast<uint32_t*>(lb + o_codes_l), frac_lists, st) != cudaSuccess)
+            if (launch_adj_build(dp, i, inst[i].n, const_cast<int32_t*>(dp.cell_cnt) + tmpl_cnt_off[t],
+                                 dp.list_base + tmpl_pbase_off[t], reinterpret_cast<uint32_t*>(lb + o_codes_l),
+                                 frac_lists, st) != cudaSuccess)
                 return PAT_ERR_CUDA;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
