@@ -104,7 +104,9 @@ typedef struct {
                          /*   (device memory ~4 B per sample), 2 = enumerate on every call    */
                          /*   (no list memory), 3 = per-cell fraction lists built at creation */
                          /*   (~12 B per sample: Mbar index and the FP32 bilinear fractions)  */
-    int32_t reserved[8];
+    int32_t abel_split;  /* CTAs (a thread-block cluster) sharing each time-stage tile: 1, 2, */
+                         /*   4 or 8; 0 = auto (more when there are fewer tiles than SMs)     */
+    int32_t reserved[7];
 } pat_options_t;
 
 /* Plan statistics (pat_plan_info). */
@@ -123,7 +125,9 @@ typedef struct {
     int32_t adj_mode;        /* adjoint gather in use: 1 = code lists, 2 = enumeration,   */
                              /*   3 = fraction lists                                      */
     int64_t list_bytes;      /* device memory of the adjoint sample lists                 */
-    int32_t reserved[4];
+    int32_t abel_split_fwd;  /* CTAs per forward / adjoint time-stage tile in use         */
+    int32_t abel_split_adj;
+    int32_t reserved[2];
 } pat_plan_info_t;
 
 /*

@@ -39,7 +39,8 @@ class PatOptions(ctypes.Structure):
     _fields_ = [
         ("image_dtype", ctypes.c_int32), ("schedule", ctypes.c_int32), ("tune", ctypes.c_int32),
         ("m_lanes", ctypes.c_int32), ("q_piece", ctypes.c_int32), ("band_rows", ctypes.c_int32),
-        ("adj_groups", ctypes.c_int32), ("adj_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8),
+        ("adj_groups", ctypes.c_int32), ("adj_mode", ctypes.c_int32), ("abel_split", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
     ]
 
 
@@ -50,7 +51,8 @@ class PatPlanInfo(ctypes.Structure):
         ("time_macs", ctypes.c_int64), ("work_units", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
         ("m_lanes", ctypes.c_int32), ("q_piece", ctypes.c_int32), ("band_rows", ctypes.c_int32),
         ("adj_groups", ctypes.c_int32), ("bands_max", ctypes.c_int32), ("adj_mode", ctypes.c_int32),
-        ("list_bytes", ctypes.c_int64), ("reserved", ctypes.c_int32 * 4),
+        ("list_bytes", ctypes.c_int64), ("abel_split_fwd", ctypes.c_int32), ("abel_split_adj", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

@@ -5,181 +5,197 @@
 //
 // P is the product-integrated Abel kernel followed by the midpoint time
 // derivative (the 2D Poisson formula of the wave problem Eq. (1)-(2)); it is
-// lower triangular plus one super-diagonal.  A CTA computes 32 outputs (one
-// per lane) for 4 detectors.  The 32-column slice of P^T (forward) or P
-// (adjoint) that the tile needs is staged in shared memory in chunks of rows
-// by 16-byte asynchronous copies spread over the CTA; the 4 detectors' rows
-// of M (or gbar) are staged by plain loads.  The 8 warps
-// split each chunk's rows and their partial sums are added in warp order
-// (deterministic).  The triangle is skipped: rows stop (forward) or start
-// (adjoint) where the tile's band of P ends.
+// lower triangular plus one super-diagonal, so a tile of outputs only needs
+// the band of the contraction where its slice of P is nonzero.
+//
+// Both stages are C[j][x] = sum_k A[j][k] B[k][x] over a 32 x 32 output tile
+// (32 detectors, 32 times or radii): A = M and B = P^T for the forward,
+// A = gbar and B = P for the adjoint.  Warp w owns detectors 4w .. 4w+3 and
+// lane l output x0 + l, so each thread keeps four FP32 accumulators and each
+// staged element of P serves 32 detectors.  Every output is a sequential
+// FMA chain over k in increasing order.
+//
+// The contraction runs in chunks of 32 rows through a ring of kStages
+// shared-memory stages filled by asynchronous copies (16-byte copies for the
+// chunk of P, 4-byte zero-filling copies that write the chunk of A already
+// transposed, so that a warp reads its four detectors as one broadcast
+// 16-byte load), kStages - 1 chunks ahead of the FMAs: a CTA's loads are all
+// in flight at once for short contractions.
+//
+// When a plan has fewer tiles than SMs, a thread-block cluster of 2 or 4 CTAs
+// shares each tile: rank r takes the r-th share of the chunks, and rank 0
+// adds the partial tiles in rank order through distributed shared memory
+// (deterministic; no global atomics).
+#include <cooperative_groups.h>
+
 #include "device_common.cuh"
 #include "kernels.h"
 
 namespace patgpu {
 
-static_assert(kAbelJ == 4, "the Abel kernels keep 4 detectors in a float4");
+namespace cg = cooperative_groups;
+
+static_assert(kAbelJ == 4 * kAbelWarps && kAbelX == kWarp && kAbelKC == 32, "Abel tile shape");
 
 namespace {
-// Adds the per-warp partials in warp order; returns the total in warp 0.
-__device__ __forceinline__ float4 reduce_warps(float4 acc, float4 (*red)[kWarp])
+constexpr int kStages = 6;
+struct AbelSmem {
+    float A[kStages][kAbelKC][kAbelJ + 4];   // [stage][k][detector], rows 16-byte aligned
+    float B[kStages][kAbelKC][kAbelX];       // [stage][k][output]
+    float part[kAbelJ][kAbelX];              // partial tile read by cluster rank 0
+};
+} // namespace
+
+// FWD: gin unused, gout = g (gsub nullable: gout = A f - gsub).
+// ADJ: gin = gbar, gout unused (writes Mbar in the plan workspace).
+template <bool FWD>
+__global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel(DevPlan dp, const float* __restrict__ gin,
+                                                             float* __restrict__ gout,
+                                                             const float* __restrict__ gsub, int cs)
 {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    red[w][lane] = acc;
-    __syncthreads();
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (w == 0) {
+    extern __shared__ __align__(16) unsigned char abel_smem[];
+    AbelSmem& sm = *reinterpret_cast<AbelSmem*>(abel_smem);
+    const int rank = (int)(blockIdx.x % (unsigned)cs);
+    const TimeTile t = (FWD ? dp.fwd_tiles : dp.adj_tiles)[blockIdx.x / cs];
+    const InstDev in = dp.inst[t.inst];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+    const float* A;   // A[j][k] with row pitch a_pitch, valid for k < a_len
+    const float* B;   // B[k][x] with row pitch b_pitch (zero padded to the chunk grid)
+    int a_pitch, a_len, b_pitch, k_begin, k_end;
+    if (FWD) {
+        A = dp.msum + in.mbar_off;
+        a_pitch = in.n_rp;
+        a_len = in.n_r;
+        B = dp.P + in.p_off + (size_t)in.n_tp * in.n_rp;
+        b_pitch = in.n_tp;
+        k_begin = 0;
+        k_end = min(in.n_r, t.x0 + kAbelX + 2);
+    } else {
+        A = gin + in.g_off;
+        a_pitch = in.n_t;
+        a_len = in.n_t;
+        B = dp.P + in.p_off;
+        b_pitch = in.n_rp;
+        k_begin = max(0, t.x0 - 2) & ~(kAbelKC - 1);
+        k_end = in.n_t;
+    }
+    const int nchunks = (k_end - k_begin + kAbelKC - 1) / kAbelKC;
+    const int per = (nchunks + cs - 1) / cs;
+    const int c_lo = min(nchunks, rank * per), c_hi = min(nchunks, c_lo + per);
+
+    // copy roles: A elements (detector ja, rows ka .. ka+3); B (row rb, columns cb .. cb+3)
+    const int ja = tid >> 3, ka = (tid & 7) * 4;
+    const int rb = tid >> 3, cb = (tid & 7) * 4;
+    const bool ja_ok = t.j0 + ja < in.n_det;
+    const float* Arow = A + (size_t)(ja_ok ? t.j0 + ja : 0) * a_pitch;
+    // issues chunk c into its stage; always commits one group (empty past the end)
+    auto issue = [&](int c) {
+        if (c < c_hi) {
+            const int st = (c - c_lo) % kStages;
+            const int k0 = k_begin + c * kAbelKC;
+            cp_async16(&sm.B[st][rb][cb], B + (size_t)(k0 + rb) * b_pitch + t.x0 + cb);
 #pragma unroll
-        for (int i = 0; i < kAbelWarps; ++i) {
-            const float4 v = red[i][lane];
-            s.x += v.x;
-            s.y += v.y;
-            s.z += v.z;
-            s.w += v.w;
+            for (int i = 0; i < 4; ++i) {
+                const int k = k0 + ka + i;
+                const bool ok = ja_ok && k < a_len;
+                cp_async4_zfill(&sm.A[st][ka + i][ja], ok ? Arow + k : Arow, ok);
+            }
+        }
+        cp_async_commit();
+    };
+
+    pdl_wait();   // M (forward) or gbar (adjoint) come from the previous kernel
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kStages - 1; ++i) issue(c_lo + i);
+    for (int c = c_lo; c < c_hi; ++c) {
+        const int st = (c - c_lo) % kStages;
+        cp_async_wait_group<kStages - 2>();   // chunk c has landed (this thread's copies)
+        __syncthreads();                      // ... and every thread's
+#pragma unroll 8
+        for (int k = 0; k < kAbelKC; ++k) {
+            const float b = sm.B[st][k][lane];
+            const float4 a = *reinterpret_cast<const float4*>(&sm.A[st][k][4 * w]);
+            acc.x = fmaf(b, a.x, acc.x);
+            acc.y = fmaf(b, a.y, acc.y);
+            acc.z = fmaf(b, a.z, acc.z);
+            acc.w = fmaf(b, a.w, acc.w);
+        }
+        __syncthreads();                      // stage st is free again
+        issue(c + kStages - 1);
+    }
+    cp_async_wait_group<0>();
+
+    if (cs > 1) {
+        cg::cluster_group cluster = cg::this_cluster();
+        sm.part[4 * w + 0][lane] = acc.x;
+        sm.part[4 * w + 1][lane] = acc.y;
+        sm.part[4 * w + 2][lane] = acc.z;
+        sm.part[4 * w + 3][lane] = acc.w;
+        cluster.sync();
+        if (rank == 0) {
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int r = 0; r < cs; ++r) {
+                const float* pr = cluster.map_shared_rank(&sm.part[0][0], r);
+                s.x += pr[(4 * w + 0) * kAbelX + lane];
+                s.y += pr[(4 * w + 1) * kAbelX + lane];
+                s.z += pr[(4 * w + 2) * kAbelX + lane];
+                s.w += pr[(4 * w + 3) * kAbelX + lane];
+            }
+            acc = s;
+        }
+        cluster.sync();   // keep every rank's partial alive until rank 0 has read it
+        if (rank != 0) return;
+    }
+
+    const float r4[4] = {acc.x, acc.y, acc.z, acc.w};
+    const int x = t.x0 + lane;
+    if (FWD) {
+        if (x < in.n_t) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = t.j0 + 4 * w + i;
+                if (j >= in.n_det) break;
+                const size_t o = in.g_off + (size_t)j * in.n_t + x;
+                const float v = r4[i] * in.inv_K;
+                gout[o] = gsub ? v - gsub[o] : v;
+            }
+        }
+    } else {
+        if (x < in.n_r) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = t.j0 + 4 * w + i;
+                if (j >= in.n_det) break;
+                dp.mbar[in.mbar_off + (size_t)j * in.n_rp + x] = r4[i];
+            }
         }
     }
-    return s;
 }
 
-// Copies rows [r0, r0 + nrows) of a 32-column slice (row pitch `pitch`
-// floats, slice starting at column c0, both multiples of 32) into
-// sP[nrows][32] with 16-byte asynchronous copies spread over the CTA.
-__device__ __forceinline__ void stage_slice(float* sP, const float* src, int pitch, int c0, int r0, int nrows)
+namespace {
+template <bool FWD>
+cudaError_t launch_abel(const DevPlan& dp, int tiles, int cs, const float* gin, float* gout, const float* gsub,
+                        cudaStream_t st)
 {
-    for (int e = threadIdx.x; e < nrows * 8; e += blockDim.x) {
-        const int r = e >> 3, c = (e & 7) * 4;
-        cp_async16(sP + r * kWarp + c, src + (size_t)(r0 + r) * pitch + c0 + c);
-    }
+    if (tiles == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_abel<FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(AbelSmem));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_abel<FWD>, dim3((unsigned)(tiles * cs)), dim3(kAbelWarps * kWarp), sizeof(AbelSmem), st, cs,
+                      dp, gin, gout, gsub, cs);
 }
 } // namespace
 
-// gsub (nullable): when given, the output is A f - gsub (the data residual).
-__global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel_fwd(DevPlan dp, float* __restrict__ g,
-                                                                 const float* __restrict__ gsub)
-{
-    extern __shared__ __align__(128) float smem_f[];
-    float* sP = smem_f;                           // [kAbelChunk][32]
-    float4* sM4 = reinterpret_cast<float4*>(smem_f + kAbelChunk * kWarp); // [kAbelChunk]
-    __shared__ float4 red[kAbelWarps][kWarp];
-    const TimeTile t = dp.fwd_tiles[blockIdx.x];
-    const InstDev in = dp.inst[t.inst];
-    const int n_r = in.n_r, n_t = in.n_t;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int kk = t.x0 + lane;
-    const int m_end = min(n_r, t.x0 + kAbelX + 2);
-    const float* PT = dp.P + in.p_off + (size_t)n_t * in.n_rp; // P^T: [m][kk], pitch n_tp
-    const float* M = dp.msum + in.mbar_off;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int mc = 0; mc < m_end; mc += kAbelChunk) {
-        const int len = min(kAbelChunk, m_end - mc);
-        __syncthreads(); // previous chunk consumed
-        stage_slice(sP, PT, in.n_tp, t.x0, mc, len);
-        for (int e = threadIdx.x; e < len; e += blockDim.x) {
-            const int m = mc + e;
-            float4 v;
-            v.x = (t.j0 + 0 < in.n_det) ? __ldg(M + (size_t)(t.j0 + 0) * in.n_rp + m) : 0.f;
-            v.y = (t.j0 + 1 < in.n_det) ? __ldg(M + (size_t)(t.j0 + 1) * in.n_rp + m) : 0.f;
-            v.z = (t.j0 + 2 < in.n_det) ? __ldg(M + (size_t)(t.j0 + 2) * in.n_rp + m) : 0.f;
-            v.w = (t.j0 + 3 < in.n_det) ? __ldg(M + (size_t)(t.j0 + 3) * in.n_rp + m) : 0.f;
-            sM4[e] = v;
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        for (int m = w; m < len; m += kAbelWarps) {
-            const float p = sP[m * kWarp + lane];
-            const float4 v = sM4[m];
-            acc.x = fmaf(p, v.x, acc.x);
-            acc.y = fmaf(p, v.y, acc.y);
-            acc.z = fmaf(p, v.z, acc.z);
-            acc.w = fmaf(p, v.w, acc.w);
-        }
-    }
-    const float4 s = reduce_warps(acc, red);
-    if (w == 0 && kk < n_t) {
-        const float sc = in.inv_K;
-        const size_t o = in.g_off + kk;
-        float* out = g + o;
-        const float r[4] = {s.x * sc, s.y * sc, s.z * sc, s.w * sc};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (t.j0 + i >= in.n_det) break;
-            const size_t jo = (size_t)(t.j0 + i) * n_t;
-            out[jo] = gsub ? r[i] - gsub[o + jo] : r[i];
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel_adj(DevPlan dp, const float* __restrict__ g)
-{
-    extern __shared__ __align__(128) float smem_f[];
-    float* sP = smem_f;                           // [kAbelChunk][32]
-    float4* sG4 = reinterpret_cast<float4*>(smem_f + kAbelChunk * kWarp); // [kAbelChunk]
-    __shared__ float4 red[kAbelWarps][kWarp];
-    const TimeTile t = dp.adj_tiles[blockIdx.x];
-    const InstDev in = dp.inst[t.inst];
-    const int n_r = in.n_r, n_t = in.n_t;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int m = t.x0 + lane;
-    const int k_begin = max(0, t.x0 - 2);
-    const float* P = dp.P + in.p_off; // [kk][m], pitch n_rp
-    const float* gi = g + in.g_off;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int kc = k_begin; kc < n_t; kc += kAbelChunk) {
-        const int len = min(kAbelChunk, n_t - kc);
-        __syncthreads();
-        stage_slice(sP, P, in.n_rp, t.x0, kc, len);
-        for (int e = threadIdx.x; e < len; e += blockDim.x) {
-            const int kk = kc + e;
-            float4 v;
-            v.x = (t.j0 + 0 < in.n_det) ? __ldg(gi + (size_t)(t.j0 + 0) * n_t + kk) : 0.f;
-            v.y = (t.j0 + 1 < in.n_det) ? __ldg(gi + (size_t)(t.j0 + 1) * n_t + kk) : 0.f;
-            v.z = (t.j0 + 2 < in.n_det) ? __ldg(gi + (size_t)(t.j0 + 2) * n_t + kk) : 0.f;
-            v.w = (t.j0 + 3 < in.n_det) ? __ldg(gi + (size_t)(t.j0 + 3) * n_t + kk) : 0.f;
-            sG4[e] = v;
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        for (int k = w; k < len; k += kAbelWarps) {
-            const float p = sP[k * kWarp + lane];
-            const float4 v = sG4[k];
-            acc.x = fmaf(p, v.x, acc.x);
-            acc.y = fmaf(p, v.y, acc.y);
-            acc.z = fmaf(p, v.z, acc.z);
-            acc.w = fmaf(p, v.w, acc.w);
-        }
-    }
-    const float4 s = reduce_warps(acc, red);
-    if (w == 0 && m < n_r) {
-        float* out = dp.mbar + in.mbar_off + m;
-        if (t.j0 + 0 < in.n_det) out[(size_t)(t.j0 + 0) * in.n_rp] = s.x;
-        if (t.j0 + 1 < in.n_det) out[(size_t)(t.j0 + 1) * in.n_rp] = s.y;
-        if (t.j0 + 2 < in.n_det) out[(size_t)(t.j0 + 2) * in.n_rp] = s.z;
-        if (t.j0 + 3 < in.n_det) out[(size_t)(t.j0 + 3) * in.n_rp] = s.w;
-    }
-}
-
-static cudaError_t set_abel_smem(const void* fn, int bytes)
-{
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
 cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st, const float* gsub)
 {
-    if (dp.n_fwd_tiles == 0) return cudaSuccess;
-    cudaError_t e = set_abel_smem(reinterpret_cast<const void*>(k_abel_fwd), dp.abel_smem_bytes);
-    if (e != cudaSuccess) return e;
-    k_abel_fwd<<<dp.n_fwd_tiles, kAbelWarps * kWarp, dp.abel_smem_bytes, st>>>(dp, g, gsub);
-    return cudaGetLastError();
+    return launch_abel<true>(dp, dp.n_fwd_tiles, dp.abel_cluster_fwd, nullptr, g, gsub, st);
 }
 
 cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st)
 {
-    if (dp.n_adj_tiles == 0) return cudaSuccess;
-    cudaError_t e = set_abel_smem(reinterpret_cast<const void*>(k_abel_adj), dp.abel_smem_bytes);
-    if (e != cudaSuccess) return e;
-    k_abel_adj<<<dp.n_adj_tiles, kAbelWarps * kWarp, dp.abel_smem_bytes, st>>>(dp, g);
-    return cudaGetLastError();
+    return launch_abel<false>(dp, dp.n_adj_tiles, dp.abel_cluster_adj, g, nullptr, nullptr, st);
 }
 
 } // namespace patgpu

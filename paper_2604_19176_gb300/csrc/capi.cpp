@@ -131,6 +131,9 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
     if (opt.band_rows != 0 && (opt.band_rows < 3 || opt.band_rows > 8192)) return PAT_ERR_INVALID_ARG;
     if (opt.adj_groups < 0 || opt.adj_groups > 16) return PAT_ERR_INVALID_ARG;
     if (opt.adj_mode < 0 || opt.adj_mode > 3) return PAT_ERR_INVALID_ARG;
+    if (opt.abel_split != 0 && opt.abel_split != 1 && opt.abel_split != 2 && opt.abel_split != 4 &&
+        opt.abel_split != 8)
+        return PAT_ERR_INVALID_ARG;
     const bool bf16 = opt.image_dtype == PAT_BF16;
     for (int i = 0; i < n_instances; ++i)
         if (!valid_geometry(geoms[i], bf16)) return PAT_ERR_INVALID_ARG;

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_wait();   // f and the work queues belong to earlier work in the stream
 
     uint32_t parity = 0;
     const int task_begin = dp.cta_seg[blockIdx.x], task_end = dp.cta_seg[blockIdx.x + 1];
@@ -225,10 +226,20 @@ cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st)
     const void* fn = circ_select(dp.m_lanes, dp.bf16 != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dp.fwd_smem_bytes);
     if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(dp.n_fwd_ctas);
+    cfg.blockDim = dim3(kCircThreads);
+    cfg.dynamicSmemBytes = (size_t)dp.fwd_smem_bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     DevPlan copy = dp;
     const void* fptr = f;
     void* args[] = {&copy, &fptr};
-    return cudaLaunchKernel(fn, dim3(dp.n_fwd_ctas), dim3(kCircThreads), args, (size_t)dp.fwd_smem_bytes, st);
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 int circmean_blocks_per_sm(int m_lanes, bool bf16, int smem_bytes)

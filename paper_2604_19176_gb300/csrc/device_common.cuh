@@ -52,6 +52,21 @@ __device__ __forceinline__ float cell_frac(float mf, float hi, float lo, float f
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Kernels of the operator chain are launched
+// with programmatic stream serialization, so the next kernel is launched as
+// soon as this one's CTAs exit (its launch overlaps the end of this one);
+// each kernel reads only the plan's immutable tables until pdl_wait, which
+// returns once the previous kernel in the stream has completed and its
+// memory is visible.  (Releasing dependents from the start of a kernel was
+// measured slower: their waiting CTAs crowd the running kernel.)  A no-op
+// without the launch attribute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // TMA (bulk async copy) and mbarrier wrappers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -123,6 +138,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void cp_async16(void* dst, const void* src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// 4-byte asynchronous copy that writes zero when !valid (nothing is read then).
+__device__ __forceinline__ void cp_async4_zfill(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all()
 {

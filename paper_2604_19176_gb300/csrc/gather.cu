@@ -120,6 +120,7 @@ __device__ __forceinline__ void release_queue(int32_t* ctr, int lane)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 5) k_adj_cells(DevPlan dp)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int G = dp.adj_groups;
     for (;;) {
@@ -224,6 +225,7 @@ __device__ __forceinline__ void list_sample(const uint32_t code, int qb, int mbq
 template <bool FRAC>
 __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
 {
+    pdl_wait();   // Mbar comes from the previous kernel; the queue from earlier calls
     const int lane = threadIdx.x & 31;
     int32_t* ctr = dp.work_counters + 2;
     const int G = dp.adj_groups;
@@ -305,6 +307,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_adj_combine(DevPlan dp, T* __restrict__ fout)
 {
     const ImgTile t = dp.img_tiles[blockIdx.x];
+    pdl_wait();
     const InstDev in = dp.inst[t.inst];
     const int n = in.n;
     const int px = t.x0 + (threadIdx.x & 31), py = t.y0 + (threadIdx.x >> 5);
@@ -361,22 +364,21 @@ cudaError_t launch_adjoint_cells(const DevPlan& dp, cudaStream_t st)
 {
     if (dp.adj_mode == 1 || dp.adj_mode == 3) {
         if (dp.n_list_items == 0) return cudaSuccess;
-        if (dp.adj_mode == 3) k_adj_list<true><<<dp.cell_blocks, 256, 0, st>>>(dp);
-        else k_adj_list<false><<<dp.cell_blocks, 256, 0, st>>>(dp);
-    } else {
-        if (dp.n_cell_items == 0) return cudaSuccess;
-        k_adj_cells<<<dp.cell_blocks, 256, 0, st>>>(dp);
+        if (dp.adj_mode == 3) return launch_pdl(k_adj_list<true>, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);
+        return launch_pdl(k_adj_list<false>, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);
     }
-    return cudaGetLastError();
+    if (dp.n_cell_items == 0) return cudaSuccess;
+    return launch_pdl(k_adj_cells, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);
 }
 
 cudaError_t launch_adjoint_gather(const DevPlan& dp, void* f, cudaStream_t st)
 {
     cudaError_t e = launch_adjoint_cells(dp, st);
     if (e != cudaSuccess) return e;
-    if (dp.bf16) k_adj_combine<__nv_bfloat16><<<dp.n_img_tiles, 256, 0, st>>>(dp, static_cast<__nv_bfloat16*>(f));
-    else k_adj_combine<float><<<dp.n_img_tiles, 256, 0, st>>>(dp, static_cast<float*>(f));
-    return cudaGetLastError();
+    if (dp.bf16)
+        return launch_pdl(k_adj_combine<__nv_bfloat16>, dim3(dp.n_img_tiles), dim3(256), 0, st, 1, dp,
+                          static_cast<__nv_bfloat16*>(f));
+    return launch_pdl(k_adj_combine<float>, dim3(dp.n_img_tiles), dim3(256), 0, st, 1, dp, static_cast<float*>(f));
 }
 
 } // namespace patgpu

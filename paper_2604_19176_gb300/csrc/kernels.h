@@ -10,6 +10,35 @@ namespace patgpu {
 
 constexpr int kCircThreads = 512;   // threads per circular-mean CTA (16 warps)
 
+// Launches fn<<<grid, block, smem, st>>>(args...) with programmatic stream
+// serialization (the kernel must call pdl_wait before it reads or writes
+// memory that earlier work in the stream touches), and optionally as
+// clusters of `cluster` CTAs along x.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cluster,
+                       Args&&... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    int na = 1;
+    if (cluster > 1) {
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = (unsigned)cluster;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        na = 2;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, fn, static_cast<KArgs>(args)...);
+}
+
 cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st);
 cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st, const float* gsub = nullptr);
 cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st);

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(256) k_tv_update(DevPlan dp, const float* __re
     __shared__ float red[8];
     const ImgTile t = dp.img_tiles[blockIdx.x];
     const InstDev in = dp.inst[t.inst];
+    pdl_wait();   // the cell sums come from the previous kernel
     const int n = in.n;
     const float* fi = f + in.f_off;
     const int j = t.x0 + (threadIdx.x & 31), i = t.y0 + (threadIdx.x >> 5);
@@ -161,9 +162,8 @@ cudaError_t launch_tv_update(const DevPlan& dp, const float* f_in, float* f_out,
                              int nonneg, float* delta, cudaStream_t st)
 {
     if (dp.n_img_tiles == 0) return cudaSuccess;
-    k_tv_update<<<dp.n_img_tiles, 256, 0, st>>>(dp, f_in, f_out, tau, lam, eps, nonneg,
-                                                delta ? dp.tv_partial : nullptr);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_tv_update, dim3(dp.n_img_tiles), dim3(256), 0, st, 1, dp, f_in, f_out, tau, lam,
+                               eps, nonneg, delta ? dp.tv_partial : nullptr);
     if (e != cudaSuccess || !delta) return e;
     k_tile_sums<<<dp.n_inst, 32, 0, st>>>(dp, dp.tv_partial, 2, delta);
     return cudaGetLastError();

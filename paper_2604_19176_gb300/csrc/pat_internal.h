@@ -137,14 +137,15 @@ struct DevPlan {
     int32_t cell_blocks;           // CTAs of the adjoint cell kernel (8 warps each)
     int32_t fwd_smem_bytes;        // dynamic shared memory of the circular-mean kernel
     int32_t fwd_rays_off;          // byte offset of the staged rays (after the largest band)
-    int32_t abel_smem_bytes;       // dynamic shared memory of the Abel kernels
+    int32_t abel_cluster_fwd;      // CTAs per cluster splitting each forward time contraction
+    int32_t abel_cluster_adj;      // the same for the adjoint time contraction
     int32_t bf16;                  // image storage is BF16
 };
 
-constexpr int kAbelJ = 4;          // detectors per Abel CTA
-constexpr int kAbelX = 32;         // outputs per Abel CTA (one per lane)
-constexpr int kAbelWarps = 8;      // warps per Abel CTA, splitting the contracted index
-constexpr int kAbelChunk = 512;    // rows of the P slice staged in shared memory at a time
+constexpr int kAbelJ = 32;         // detectors per Abel tile (4 per warp)
+constexpr int kAbelX = 32;         // outputs per Abel tile (one per lane)
+constexpr int kAbelWarps = 8;      // warps per Abel CTA
+constexpr int kAbelKC = 32;        // contraction rows staged per pipeline stage
 
 // Shared-memory row pitch (elements) of a band of an N-wide image.  The
 // pitch leaves a zero column on each side, keeps rows 16-byte aligned, and is

@@ -234,16 +234,17 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     for (int i = 0; i < n_inst; ++i) {
         const int nt = geoms[i].n_t;
         if (!p_off.count(nt)) {
-            // P (nt rows, pitch nrp) then P^T (nr rows, pitch ntp); padding is zero
+            // P (ntp rows, pitch nrp) then P^T (nrp rows, pitch ntp); padding is
+            // zero, so the time kernels' 32-row chunks never leave the matrix
             p_off[nt] = (int64_t)pmat.size();
             const int nr = nt + 2, nrp = (nr + 31) & ~31, ntp = (nt + 31) & ~31;
             std::vector<float> Pm = build_abel_matrix(nt);
             const size_t base = pmat.size();
-            pmat.resize(base + (size_t)nt * nrp + (size_t)nr * ntp, 0.0f);
+            pmat.resize(base + 2 * (size_t)ntp * nrp, 0.0f);
             for (int kk = 0; kk < nt; ++kk)
                 for (int m = 0; m < nr; ++m) {
                     pmat[base + (size_t)kk * nrp + m] = Pm[(size_t)kk * nr + m];
-                    pmat[base + (size_t)nt * nrp + (size_t)m * ntp + kk] = Pm[(size_t)kk * nr + m];
+                    pmat[base + (size_t)ntp * nrp + (size_t)m * ntp + kk] = Pm[(size_t)kk * nr + m];
                 }
         }
     }
@@ -605,9 +606,19 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (int kk = 0; kk < d.n_t; ++kk) nnz += std::min(kk + 3, d.n_r);
         time_macs += nnz * d.n_det;
     }
-    // larger Abel tiles first (the triangle makes late time tiles heavier)
-    std::stable_sort(fwd_tiles.begin(), fwd_tiles.end(), [](const TimeTile& a, const TimeTile& b) { return a.x0 > b.x0; });
-    std::stable_sort(adj_tiles.begin(), adj_tiles.end(), [](const TimeTile& a, const TimeTile& b) { return a.x0 < b.x0; });
+    // longest contractions first (the triangle makes late forward tiles and
+    // early adjoint tiles heavier)
+    auto fwd_len = [&](const TimeTile& t) { return std::min(inst[t.inst].n_r, t.x0 + kAbelX + 2); };
+    auto adj_len = [&](const TimeTile& t) { return inst[t.inst].n_t - std::max(0, t.x0 - 2); };
+    std::stable_sort(fwd_tiles.begin(), fwd_tiles.end(),
+                     [&](const TimeTile& a, const TimeTile& b) { return fwd_len(a) > fwd_len(b); });
+    std::stable_sort(adj_tiles.begin(), adj_tiles.end(),
+                     [&](const TimeTile& a, const TimeTile& b) { return adj_len(a) > adj_len(b); });
+    // with fewer tiles than SMs, a cluster of CTAs splits each contraction
+    auto cluster_for = [&](size_t tiles) {
+        if (opt.abel_split > 0) return (int)opt.abel_split;
+        return tiles >= (size_t)P.num_sms ? 1 : tiles * 2 >= (size_t)P.num_sms ? 2 : 4;
+    };
 
     // ---- upload -----------------------------------------------------------
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -716,7 +727,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.cell_blocks = cell_blocks;
     dp.fwd_smem_bytes = smem_bytes;
     dp.fwd_rays_off = band_bytes;
-    dp.abel_smem_bytes = kAbelChunk * kWarp * (int)sizeof(float) + kAbelChunk * (int)sizeof(float4);
+    dp.abel_cluster_fwd = cluster_for(fwd_tiles.size());
+    dp.abel_cluster_adj = cluster_for(adj_tiles.size());
     dp.bf16 = bf16 ? 1 : 0;
 
     // ---- sample count (exact, with the kernels' FP32 arithmetic) ----------
@@ -879,6 +891,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (auto& b : T.bands) I.band_rows = std::max(I.band_rows, b.hi - b.lo + 1);
     I.adj_groups = dp.adj_groups;
     I.adj_mode = dp.adj_mode == 0 ? 2 : dp.adj_mode;
+    I.abel_split_fwd = dp.abel_cluster_fwd;
+    I.abel_split_adj = dp.abel_cluster_adj;
     I.list_bytes = list_bytes;
     I.device_bytes += list_bytes;
     I.bands_max = bands_max;

@@ -2,8 +2,9 @@
 //
 // Candidates for the circular-mean kernel (radii per warp, angles per unit,
 // rows per shared-memory band) are timed on the plan's own geometries with
-// CUDA events, then candidates for the adjoint gather (detector groups) with
-// the best forward shape; the fastest plan is kept.  Results are cached per
+// CUDA events, then the cluster split of the two time stages, then candidates
+// for the adjoint gather (list format, list parts) with the best shapes so
+// far; the fastest plan is kept.  Results are cached per
 // process by geometry list and image dtype, so a second plan with the same
 // geometries skips the search.
 #include <algorithm>
@@ -164,6 +165,27 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
                 }
             }
         }
+    }
+    // ---- time-stage cluster split (with the best forward shape) ------------
+    if (opt.abel_split == 0) {
+        best_ms = 1e30f;
+        pat_options_t split_opt = best_opt;
+        for (int cs : {1, 2, 4, 8}) {
+            pat_options_t o = best_opt;
+            o.abel_split = cs;
+            Plan* p = try_build(geoms, n_inst, o, st);
+            if (!p) continue;
+            const float ms = time_ms(st, 2, 5, [&] {
+                cudaError_t e = launch_abel_fwd(p->dp, d_g, st);
+                return e == cudaSuccess ? launch_abel_adj(p->dp, d_g, st) : e;
+            });
+            drop(p);
+            if (ms > 0.f && ms < best_ms) {
+                best_ms = ms;
+                split_opt = o;
+            }
+        }
+        best_opt = split_opt;
     }
     // ---- adjoint candidates (with the best forward shape) ------------------
     best_ms = 1e30f;

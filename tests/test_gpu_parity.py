@@ -79,7 +79,8 @@ def test_forward_adjoint_vessel256_full_size(cuda_dev):
 @pytest.mark.parametrize("kw", [dict(m_lanes=16), dict(m_lanes=8), dict(q_piece=4), dict(band_rows=5),
                                 dict(band_rows=17, m_lanes=8, q_piece=12), dict(adj_groups=1, adj_mode=2), dict(adj_groups=3, adj_mode=2),
                                 dict(adj_groups=16, adj_mode=2), dict(adj_mode=1), dict(adj_mode=1, adj_groups=3),
-                                dict(adj_mode=3), dict(adj_mode=3, adj_groups=5), dict(tune=1)])
+                                dict(adj_mode=3), dict(adj_mode=3, adj_groups=5), dict(abel_split=1),
+                                dict(abel_split=2), dict(abel_split=8), dict(tune=1)])
 def test_tile_shapes_agree_with_oracle(cuda_dev, kw):
     g = Geometry(48, 24, 0.4, 1.3 * math.pi, 80, 2.0, 70)
     f = f32(inputs.gaussian_phantom(48, 5, seed=3) + 0.1 * inputs.random_image(48, seed=4))
