@@ -341,7 +341,68 @@ def run_extras(dev, flush, with_oracle: bool = True) -> dict:
     out["batch64_uneven"] = {"instances_per_s": 64 * 1000.0 / msb, "ms_per_batch": msb,
                              "samples": pb.info()["samples"], "graph": "forward + adjoint, one replay"}
     del op, pb
+    torch.cuda.empty_cache()
+    out["precision_1024_b8"] = precision_study(dev, stream, flush, with_oracle)
     return out
+
+
+def precision_study(dev, stream, flush, with_oracle: bool) -> dict:
+    """BF16 vs FP32 image storage on the 1024^2 x 8 workload (forward + adjoint
+    of the batch), with the error of each against the FP64 oracle on a 256^2
+    replica: the same analytic phantom (same seed, same physical tube widths),
+    the same 512 detectors on 270 degrees, time grid and angular rule."""
+    import torch
+
+    from paper_2604_19176_gb300 import Geometry, PatPlan, inputs, workloads
+
+    wl = workloads.vessel1024_b8()
+    geoms = list(wl.geometries)
+    phs = np.stack(wl.phantoms())
+    res = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        pp = PatPlan(geoms, device=dev, image_dtype=dt)
+        ft = torch.tensor(phs, dtype=dt, device=dev)
+        go = torch.empty(pp.data_shape(), device=dev)
+        fo = torch.empty(pp.image_shape(), dtype=dt, device=dev)
+
+        def fa():
+            pp.forward(ft, out=go)
+            pp.adjoint(go, out=fo)
+
+        ms = _time_steps(fa, stream, flush, 5, warmup=2)
+        res[name] = {"instance_apps_per_s": len(geoms) * 1000.0 / ms, "ms_per_batch": ms,
+                     "samples_per_instance": pp.info()["samples"] // len(geoms)}
+        del pp, ft, go, fo
+        torch.cuda.empty_cache()
+    g = geoms[0]
+    gr = Geometry(256, g.n_det, g.arc_start, g.arc_span, g.n_t, g.t_max, g.n_angles)
+    p = wl.params
+    f_r = inputs.mixed_phantom(256, p["tubes"], p["gaussians"], seed=p["seeds"][0],
+                               width_px=tuple(w * 256 / g.n for w in p["width_px"]))
+    d_r = inputs.random_data(gr.n_det, gr.n_t, seed=6)
+    outs = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        pr = PatPlan(gr, device=dev, image_dtype=dt)
+        fw = pr.forward(torch.tensor(f_r, dtype=dt, device=dev))
+        ad = pr.adjoint(torch.tensor(d_r, dtype=torch.float32, device=dev))
+        torch.cuda.synchronize()
+        outs[name] = (fw.double().cpu().numpy(), ad.double().cpu().numpy())
+        del pr
+    if with_oracle:
+        import oracle as O
+
+        O.set_threads(os.cpu_count() or 1)
+        og = O.Geometry(gr.n, gr.n_det, gr.arc_start, gr.arc_span, gr.n_t, gr.t_max, gr.n_angles)
+        ref_f = O.forward(og, f_r.astype(np.float32).astype(np.float64))
+        ref_a = O.adjoint(og, d_r.astype(np.float32).astype(np.float64))
+        O.set_threads(1)
+        for name, (fw, ad) in outs.items():
+            res[name]["rel_l2_fwd_vs_fp64_replica256"] = float(np.linalg.norm(fw - ref_f) / np.linalg.norm(ref_f))
+            res[name]["rel_l2_adj_vs_fp64_replica256"] = float(np.linalg.norm(ad - ref_a) / np.linalg.norm(ref_a))
+    res["config"] = ("8 x 1024^2 (40 tubes 2-6 px + 10 Gaussians, seeds 5..12), 512 detectors / 270 deg, "
+                     "n_t 2048, K 2048; replica 256^2 of seed 5 with the same physical tube widths; adjoint "
+                     "error on N(0,1) data")
+    return res
 
 
 # --------------------------------------------------------------------------

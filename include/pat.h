@@ -99,7 +99,7 @@ typedef struct {
     int32_t q_piece;     /* max angular nodes per work unit (multiple of 4); 0 = auto        */
     int32_t band_rows;   /* max image rows per shared-memory band; 0 = auto                  */
     int32_t adj_groups;  /* detector groups of the adjoint gather, 1..16; 0 = auto           */
-    int32_t adj_mode;    /* adjoint gather: 0 = auto (3 if it fits the list budget, else 1,   */
+    int32_t adj_mode;    /* adjoint gather: 0 = auto (1 if it fits the list budget, else 3,   */
                          /*   else 2), 1 = per-cell sample code lists built at creation       */
                          /*   (device memory ~4 B per sample), 2 = enumerate on every call    */
                          /*   (no list memory), 3 = per-cell fraction lists built at creation */

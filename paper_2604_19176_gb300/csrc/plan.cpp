@@ -511,16 +511,17 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     // the forward's evaluated-sample upper bound); its groups split each list
     int64_t slot_samples_all = 0;
     for (int i = 0; i < n_inst; ++i) slot_samples_all += tmpls[inst_tmpl[i]].slot_samples;
-    // fraction lists (12 B per sample) when they fit the budget, else packed
-    // codes (4 B per sample, when the code bits fit), else enumeration
+    // packed code lists (4 B per sample) when the code bits and the budget
+    // allow (the fastest form measured), else fraction lists (12 B per
+    // sample), else enumeration on every call
     const bool codes_fit = P.code_bits_max <= 32;
     if (opt.adj_mode == 1 && !codes_fit) return PAT_ERR_UNSUPPORTED;
     int list_mode = opt.adj_mode;
     if (list_mode == 0) {
         const double budget = (double)P.list_budget_bytes;
-        list_mode = (double)slot_samples_all * 12.0 <= budget                ? 3
-                    : codes_fit && (double)slot_samples_all * 4.0 <= budget ? 1
-                                                                            : 2;
+        list_mode = codes_fit && (double)slot_samples_all * 4.0 <= budget ? 1
+                    : (double)slot_samples_all * 12.0 <= budget            ? 3
+                                                                           : 2;
     }
     const bool use_lists = list_mode == 1 || list_mode == 3;
     const bool frac_lists = list_mode == 3;
@@ -734,12 +735,25 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     // ---- sample count (exact, with the kernels' FP32 arithmetic) ----------
     unsigned long long* d_count = reinterpret_cast<unsigned long long*>(base + o_count);
     if (cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st) != cudaSuccess) return PAT_ERR_CUDA;
-    for (int i = 0; i < n_inst; ++i)
-        if (launch_count_samples(dp, i, inst[i].n_det, d_count, st) != cudaSuccess) return PAT_ERR_CUDA;
+    // once per geometry template (identical instances have identical counts)
     unsigned long long count = 0;
-    if (cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return PAT_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
+    {
+        std::vector<int> mult(tmpls.size(), 0), first(tmpls.size(), -1);
+        for (int i = 0; i < n_inst; ++i) {
+            if (first[inst_tmpl[i]] < 0) first[inst_tmpl[i]] = i;
+            ++mult[inst_tmpl[i]];
+        }
+        for (size_t t = 0; t < tmpls.size(); ++t) {
+            const int i = first[t];
+            unsigned long long c = 0;
+            if (cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st) != cudaSuccess ||
+                launch_count_samples(dp, i, inst[i].n_det, d_count, st) != cudaSuccess ||
+                cudaMemcpyAsync(&c, d_count, sizeof(c), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return PAT_ERR_CUDA;
+            count += c * (unsigned long long)mult[t];
+        }
+    }
 
     // ---- adjoint sample lists (list mode) --------------------------------------
     // Hits are counted per cell, then stored per (8 x 4 patch, part): the 32

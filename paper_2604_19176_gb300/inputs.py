@@ -92,13 +92,25 @@ def _render_tube(n: int, poly: np.ndarray, half_width: float, amp: float, out: n
     PY = ys[:, :, None, None]  # (ny, 4, 1, 1)
     d2 = np.full((ys.shape[0], 4, xs.shape[0], 4), np.inf)
     for a, b in zip(poly[:-1], poly[1:]):
+        # only the segment's own box (widened by the half width) can be within
+        # half_width of it, so the coverage test below sees the same answer
+        slo = np.minimum(a, b) - half_width - h
+        shi = np.maximum(a, b) + half_width + h
+        sx0 = max(int(math.floor((slo[0] + 1) / h)), ix0) - ix0
+        sx1 = min(int(math.ceil((shi[0] + 1) / h)), ix1) - ix0
+        sy0 = max(int(math.floor((slo[1] + 1) / h)), iy0) - iy0
+        sy1 = min(int(math.ceil((shi[1] + 1) / h)), iy1) - iy0
+        if sx0 >= sx1 or sy0 >= sy1:
+            continue
+        px, py = PX[:, :, sx0:sx1, :], PY[sy0:sy1]
         ab = b - a
         L2 = float(ab @ ab)
-        t = ((PX - a[0]) * ab[0] + (PY - a[1]) * ab[1]) / L2
+        t = ((px - a[0]) * ab[0] + (py - a[1]) * ab[1]) / L2
         t = np.clip(t, 0.0, 1.0)
-        dx = PX - (a[0] + t * ab[0])
-        dy = PY - (a[1] + t * ab[1])
-        d2 = np.minimum(d2, dx * dx + dy * dy)
+        dx = px - (a[0] + t * ab[0])
+        dy = py - (a[1] + t * ab[1])
+        blk = d2[sy0:sy1, :, sx0:sx1, :]
+        np.minimum(blk, dx * dx + dy * dy, out=blk)
     cover = (d2 <= half_width * half_width).mean(axis=(1, 3))
     np.maximum(out[iy0:iy1, ix0:ix1], amp * cover, out=out[iy0:iy1, ix0:ix1])
 
