@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--profile", action="store_true", help="short run for ncu captures (no flush, no extras)")
+    p.add_argument("--tile", default="",
+                   help="fixed tile shape m_lanes,q_piece,band_rows,adj_groups,adj_mode,abel_split instead of "
+                        "the autotuner (e.g. the tile_shape a previous run reported), for reproducible profiles")
     return p.parse_args()
 
 
@@ -426,7 +429,12 @@ def main():
     from paper_2604_19176_gb300 import PatPlan, inputs
 
     wl, g, f_true = make_inputs(seed_offset=rank)
-    plan = PatPlan(g, device=dev, tune=1)  # autotuned tile shapes (timed at plan creation)
+    if args.tile:
+        ml, qp, br, ag, am, sp = (int(x) for x in args.tile.split(","))
+        plan = PatPlan(g, device=dev, m_lanes=ml, q_piece=qp, band_rows=br, adj_groups=ag, adj_mode=am,
+                       abel_split=sp)
+    else:
+        plan = PatPlan(g, device=dev, tune=1)  # autotuned tile shapes (timed at plan creation)
     info = plan.info()
     stream = torch.cuda.current_stream(dev)
 
@@ -581,7 +589,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * n_steps,
                 "tile_shape": {k: info[k] for k in ("m_lanes", "q_piece", "band_rows", "bands_max", "adj_groups",
-                                                    "adj_mode")},
+                                                    "adj_mode", "abel_split_fwd", "abel_split_adj")},
                 "samples_per_application": samples, "sample_slots": info["sample_slots"],
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
                 "extras": extras}
