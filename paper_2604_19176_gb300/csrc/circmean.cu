@@ -98,11 +98,11 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
             const int ri = i / (pad + CO), c = i - ri * (pad + CO);
             s[ri * W + (c < CO ? c : n + c)] = zero;
         }
-        for (int ri = 0; ri < rows; ++ri) {
-            const int r = sg.band_lo + ri;
-            if (r >= 0 && r < n) continue;
-            for (int c = threadIdx.x; c < n; c += blockDim.x) s[ri * W + CO + c] = zero;
-        }
+        // only the first band row (-1) and the last (n) can lie outside the image
+        if (sg.band_lo < 0)
+            for (int c = threadIdx.x; c < n; c += blockDim.x) s[CO + c] = zero;
+        if (sg.band_hi >= n)
+            for (int c = threadIdx.x; c < n; c += blockDim.x) s[(n - sg.band_lo) * W + CO + c] = zero;
         __syncthreads();
         if (!mbar_wait_bounded(&bar, parity, dp.status, 1)) {
             mbar_wait_bounded(&bar, parity, dp.status, 1); // let copies in flight land before exiting
@@ -117,6 +117,40 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
         const float4* det = dp.det + in.det_off;
         const Unit* units = dp.units + sg.unit_begin;
         int32_t* queue = dp.work_counters + kCircQueueBase + 2 * sg.queue;
+
+        const size_t plane = (size_t)in.n_det * in.n_r;
+        const int32_t* slotcnt = reinterpret_cast<const int32_t*>(dp.slotcnt + in.slotcnt_off);
+        // The last unit of (j, radius block) to arrive sums the block's slots in
+        // slot order (deterministic) into M and re-arms the counter.
+        // blocks are j * nmb + m0 / ML; this lane's radius in a block is m0 + ml
+        int p_blk = -1;                  // slot written, arrival not yet counted
+        int q_blk = -1, q_total = 0;     // arrival counted, result pending (lane 0)
+        int q_ret = 0;
+        auto resolve = [&]() {
+            const int last = __shfl_sync(0xffffffffu, q_ret == q_total - 1 ? 1 : 0, 0);
+            if (last) {
+                __threadfence();
+                const int q_j = q_blk / in.nmb, q_m = (q_blk - q_j * in.nmb) * ML + ml;
+                if (ql == 0 && q_m < in.n_r) {
+                    const float* sl0 = dp.mpart + in.mpart_off + (size_t)q_j * in.n_r + q_m;
+                    // four slots' loads in flight at a time, added in slot order
+                    float sum = 0.f;
+                    int sl = 0;
+                    for (; sl + 4 <= q_total; sl += 4) {
+                        const float a0 = __ldcg(sl0 + (size_t)sl * plane), a1 = __ldcg(sl0 + (size_t)(sl + 1) * plane);
+                        const float a2 = __ldcg(sl0 + (size_t)(sl + 2) * plane), a3 = __ldcg(sl0 + (size_t)(sl + 3) * plane);
+                        sum += a0;
+                        sum += a1;
+                        sum += a2;
+                        sum += a3;
+                    }
+                    for (; sl < q_total; ++sl) sum += __ldcg(sl0 + (size_t)sl * plane);
+                    dp.msum[in.mbar_off + (size_t)q_j * in.n_rp + q_m] = sum;
+                }
+                if (lane == 0) dp.slot_arrivals[in.arrive_off + q_blk] = 0;
+            }
+            q_blk = -1;
+        };
 
         int u = 0;
         if (lane == 0) u = atomicAdd(queue, 1);
@@ -151,28 +185,29 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
             float acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
             for (int o = ML; o < kWarp; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            const size_t plane = (size_t)in.n_det * in.n_r;
-            float* slots = dp.mpart + in.mpart_off + (size_t)un.j * in.n_r;
-            if (ql == 0 && m < in.n_r) slots[(size_t)un.slot * plane + m] = acc;
-            // The last unit of (j, radius block) to finish sums the block's slots in
-            // slot order (deterministic) into M and re-arms the counter.
-            __threadfence();
-            const int blk = un.j * in.nmb + un.m0 / ML;
-            const int total = reinterpret_cast<const int32_t*>(dp.slotcnt + in.slotcnt_off)[blk];
-            int last = 0;
-            if (lane == 0) last = (atomicAdd(dp.slot_arrivals + in.arrive_off + blk, 1) == total - 1);
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last) {
+            // Pipelined arrival: the arrival counted for the unit before last
+            // is resolved now (its atomic returned while this unit was sampled),
+            // the previous unit's arrival is issued now (its slot write has
+            // drained, so the fence is cheap), and this unit's slot is written.
+            if (q_blk >= 0) resolve();
+            if (p_blk >= 0) {
                 __threadfence();
-                if (ql == 0 && m < in.n_r) {
-                    float sum = 0.f;
-                    for (int sl = 0; sl < total; ++sl) sum += __ldcg(slots + (size_t)sl * plane + m);
-                    dp.msum[in.mbar_off + (size_t)un.j * in.n_rp + m] = sum;
-                }
-                if (lane == 0) dp.slot_arrivals[in.arrive_off + blk] = 0;
+                q_blk = p_blk;
+                q_total = slotcnt[p_blk];
+                if (lane == 0) q_ret = atomicAdd(dp.slot_arrivals + in.arrive_off + p_blk, 1);
             }
+            if (ql == 0 && m < in.n_r) dp.mpart[in.mpart_off + (size_t)un.slot * plane + (size_t)un.j * in.n_r + m] = acc;
+            p_blk = un.j * in.nmb + un.m0 / ML;
             u = u2;
             un = un2;
+        }
+        if (q_blk >= 0) resolve();
+        if (p_blk >= 0) {
+            __threadfence();
+            q_blk = p_blk;
+            q_total = slotcnt[p_blk];
+            if (lane == 0) q_ret = atomicAdd(dp.slot_arrivals + in.arrive_off + p_blk, 1);
+            resolve();
         }
         // this CTA is done with the band task; its last participant re-arms the queue
         __syncthreads();

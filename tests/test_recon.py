@@ -74,12 +74,17 @@ def test_tv_autograd_matches_oracle(cuda_dev):
         _, rg = O.tv(imgs[i].astype(np.float64), 1e-2)
         got = f.grad[i].double().cpu().numpy()
         assert np.linalg.norm(got - float(w[i]) * rg) / np.linalg.norm(float(w[i]) * rg) <= 1e-5
-    # directional central difference of the GPU TV value itself (FP32, step 1e-2)
-    v = torch.tensor(inputs.random_image(32, seed=7), dtype=torch.float32, device=cuda_dev).expand(2, 32, 32)
+    # directional central difference of the GPU TV value itself (FP32): smooth
+    # images, eps = 0.1 and step 1e-2 keep the FP32 rounding of the difference
+    # quotient near 3e-4 (measured on a CPU emulation of the same sums)
+    sm = np.stack([inputs.gaussian_phantom(32, 3, seed=5), inputs.vessel_phantom(32, 4, seed=5)]).astype(np.float32)
+    fs = torch.tensor(sm, device=cuda_dev, requires_grad=True)
+    (tv_value(fs, plan, 0.1) * w).sum().backward()
+    v = torch.tensor(inputs.gaussian_phantom(32, 4, seed=9), dtype=torch.float32, device=cuda_dev).expand(2, 32, 32)
     with torch.no_grad():
         t = 1e-2
-        fd = ((tv_value(f + t * v, plan, 1e-2) - tv_value(f - t * v, plan, 1e-2)).double() / (2 * t)) @ w.double()
-    dd = float((f.grad.double() * v.double()).sum())
+        fd = ((tv_value(fs + t * v, plan, 0.1) - tv_value(fs - t * v, plan, 0.1)).double() / (2 * t)) @ w.double()
+    dd = float((fs.grad.double() * v.double()).sum())
     assert abs(float(fd) - dd) <= 2e-3 * abs(dd)
 
 
