@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
         const unsigned uw = (unsigned)n, vw = (unsigned)(sg.band_hi - 1 - sg.band_lo);
         const float4* det = dp.det + in.det_off;
         const Unit* units = dp.units + sg.unit_begin;
-        int32_t* queue = dp.work_counters + kCircQueueBase + 2 * sg.queue;
+        int32_t* queue = dp.work_counters + (2 + sg.queue) * kQueueStride;
 
         const size_t plane = (size_t)in.n_det * in.n_r;
         const int32_t* slotcnt = reinterpret_cast<const int32_t*>(dp.slotcnt + in.slotcnt_off);

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
 {
     pdl_wait();   // Mbar comes from the previous kernel; the queue from earlier calls
     const int lane = threadIdx.x & 31;
-    int32_t* ctr = dp.work_counters + 2;
+    int32_t* ctr = dp.work_counters + kQueueStride;
     const int G = dp.adj_groups;
     for (;;) {
         const int item = take_item(ctr, lane);

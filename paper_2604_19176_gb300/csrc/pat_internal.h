@@ -39,7 +39,12 @@ constexpr int kColOff = 4;        // FP32 shared image: column 0 at word offset 
 constexpr int kColOffBF16 = 8;    // BF16 shared image: column 0 at element offset 8 (16 B aligned)
 constexpr int kPatchW = 8;        // adjoint: one warp owns an 8 x 4 patch of cells
 constexpr int kPatchH = 4;
-constexpr int kCircQueueBase = 4; // work_counters[4 + 2 t], [5 + 2 t]: queue of circular-mean band task t
+// Work queues live kQueueStride ints apart (one 128-byte line each, so that
+// queues taken by different CTAs do not serialise on one L2 line): queue 0 is
+// the adjoint cell kernel's, queue 1 the adjoint list kernel's, queue 2 + t
+// circular-mean band task t's.  Each queue is two ints: the next item and the
+// count of finished participants.
+constexpr int kQueueStride = 32;
 
 // Per-instance descriptor (device resident, read by every kernel).
 struct InstDev {
@@ -124,8 +129,7 @@ struct DevPlan {
     float* mpart;                  // forward partial slots
     float* msum;                   // forward circular-mean sums M (same layout as Mbar)
     int32_t* slot_arrivals;        // per (detector, radius block): units finished this call
-    int32_t* work_counters;        // dynamic work queues: [0..1] adjoint cells, [2..3] adjoint lists,
-                                   // then two per circular-mean band task
+    int32_t* work_counters;        // dynamic work queues, kQueueStride ints apart (see kQueueStride)
     float* mbar;                   // adjoint Mbar
     float4* zbuf;                  // adjoint per-group cell sums
     float* tv_partial;             // per image tile partial sums

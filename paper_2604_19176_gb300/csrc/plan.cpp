@@ -675,8 +675,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const int64_t tv_parts = 2 * (int64_t)itiles.size();
     const int64_t o_msum = mpart_total, o_mbar = o_msum + mbar_total, o_tvp = o_mbar + mbar_total;
     const int64_t o_arr = o_tvp + tv_parts;
-    const int64_t o_ctr = o_arr + arrive_total;
-    const int64_t n_ctr = kCircQueueBase + 2 * n_band_tasks;
+    const int64_t o_ctr = ((o_arr + arrive_total + kQueueStride - 1) / kQueueStride) * kQueueStride;
+    const int64_t n_ctr = (2 + (int64_t)n_band_tasks) * kQueueStride;
     const int64_t o_res = ((o_ctr + n_ctr + 63) / 64) * 64;   // data residual of pat_tv_step
     const int64_t z_float_off = ((o_res + P.g_offsets[n_inst] + 63) / 64) * 64;
     P.work_floats = z_float_off + 4 * z_total;
