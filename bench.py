@@ -44,7 +44,7 @@ SMEM_BYTES_PER_CLK_SM = 128        # shared-memory load bandwidth per SM per clo
 BYTES_PER_SAMPLE = 16              # 4 FP32 texels per bilinear sample
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=2000)
@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--tile", default="",
                    help="fixed tile shape m_lanes,q_piece,band_rows,adj_groups,adj_mode,abel_split instead of "
                         "the autotuner (e.g. the tile_shape a previous run reported), for reproducible profiles")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def dist_env():
@@ -64,6 +64,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's step time (every rank gets it); ranks run independent
+    instances, so the job is as fast as its slowest rank."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def job_value(ms: float, world: int) -> float:
+    """Whole-job throughput: one application per rank per step of `ms`."""
+    return world * 1000.0 / ms
 
 
 # --------------------------------------------------------------------------
@@ -199,9 +217,9 @@ def reference_arm(args):
     # each step: a bounded sample of A + A^T, scaled to one application
     cores = os.cpu_count() or 1
     per = []
-    for _ in range(args.warmup):
-        pass
     budget = max(2.0, min(20.0, 120.0 / max(1, args.steps)))
+    if args.warmup > 0:
+        cpu_oracle_timing(g, f_true, budget_s=0.5)   # one short untimed sample (builds and loads the oracle)
     steps = min(args.steps, 10)
     for _ in range(steps):
         r = cpu_oracle_timing(g, f_true, budget_s=budget / 4)
@@ -502,12 +520,8 @@ def main():
     torch.cuda.synchronize()
     plan.set_timing(False)
     ktimes = plan.kernel_times()
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t)
-    value = world * 1000.0 / ms
+    ms = max_over_ranks(statistics.mean(step_ms), world, dev)
+    value = job_value(ms, world)
 
     # ---- roofline of the dominant kernel --------------------------------
     peaks, peak_kind = load_peaks()
@@ -564,8 +578,8 @@ def main():
             b.synchronize()
             if i >= 3:
                 e_ms.append(a.elapsed_time(b))
-        em = statistics.mean(e_ms)
-        e2e = {"value": world * 1000.0 / em, "unit": UNIT,
+        em = max_over_ranks(statistics.mean(e_ms), world, dev)
+        e2e = {"value": job_value(em, world), "unit": UNIT,
                "h2d_bytes_per_step": int(h_f.numel() * 4 + h_g.numel() * 4),
                "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": em,
                "note": "pinned host f and g copied in, A f and A^T g, A^T g copied out, per step"}
