@@ -71,10 +71,14 @@ typedef enum {
 
 typedef enum { PAT_F32 = 0, PAT_BF16 = 1 } pat_dtype_t;
 
-/* Schedules for pat_forward / pat_adjoint. */
+/* Schedules for pat_forward / pat_adjoint.  Only PAT_SCHED_STAGED is built:
+ * every stage is already one persistent (or tile-indexed) launch over all
+ * instances of a plan, and a whole operator call can be captured in one CUDA
+ * graph by the caller.  PAT_SCHED_PERSISTENT (a single fused launch per
+ * operator) is reserved and returns PAT_ERR_UNSUPPORTED. */
 typedef enum {
-    PAT_SCHED_STAGED = 0,     /* one launch per stage (circular means, time)   */
-    PAT_SCHED_PERSISTENT = 1  /* one persistent launch per operator (batched) */
+    PAT_SCHED_STAGED = 0,     /* one launch per stage (circular means, time, gather) */
+    PAT_SCHED_PERSISTENT = 1  /* reserved                                            */
 } pat_schedule_t;
 
 /* One acquisition geometry (one instance). */

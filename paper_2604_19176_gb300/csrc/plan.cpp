@@ -146,9 +146,7 @@ struct GeomKey {
 
 struct BandTemplate {
     int lo, hi;                      // cell rows [lo, hi)
-    std::vector<Unit> units;         // reordered into segments
-    std::vector<std::pair<int, int>> seg_ranges; // [begin, end) within units
-    std::vector<double> seg_cost;
+    std::vector<Unit> units;         // the band's units, largest first
     double cost = 0.0;
 };
 
@@ -157,8 +155,7 @@ struct GeomTemplate {
     std::vector<int32_t> slotcnt;    // n_det x nmb
     int n_slots = 0;
     int nmb = 0;
-    int64_t unit_base = 0;           // offset of band 0's units in the global unit array
-    std::vector<int64_t> band_unit_base;
+    std::vector<int64_t> band_unit_base; // offset of each band's units in the global unit array
     int64_t slot_samples = 0;        // lane-samples the circular-mean kernel evaluates
 };
 
