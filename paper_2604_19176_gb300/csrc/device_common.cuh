@@ -67,6 +67,38 @@ __device__ __forceinline__ void pdl_wait()
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint value of one pixel before the 1/K: over the cell-sum parts, Z00 of
+// its own cell, Z10 of the cell to its left, Z01 of the cell below and Z11 of
+// the diagonal one (float4 offsets within a part plane of `plane` cells).
+// The loads of four parts are in flight together; the additions keep part
+// order (the result does not depend on the batching).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float corner_sum(const float4* __restrict__ z, size_t plane, int parts, size_t c_self,
+                                            size_t c_left, size_t c_down, size_t c_diag)
+{
+    float s = 0.f;
+    int g = 0;
+    for (; g + 4 <= parts; g += 4) {
+        float v[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4* zg = z + (size_t)(g + u) * plane;
+            v[u][0] = __ldg(&zg[c_self].x);
+            v[u][1] = __ldg(&zg[c_left].y);
+            v[u][2] = __ldg(&zg[c_down].z);
+            v[u][3] = __ldg(&zg[c_diag].w);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s += v[u][0] + v[u][1] + v[u][2] + v[u][3];
+    }
+    for (; g < parts; ++g) {
+        const float4* zg = z + (size_t)g * plane;
+        s += __ldg(&zg[c_self].x) + __ldg(&zg[c_left].y) + __ldg(&zg[c_down].z) + __ldg(&zg[c_diag].w);
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
 // TMA (bulk async copy) and mbarrier wrappers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p)

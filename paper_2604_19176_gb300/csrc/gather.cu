@@ -315,13 +315,9 @@ __global__ void __launch_bounds__(256) k_adj_combine(DevPlan dp, T* __restrict__
     const int w = n + 1;
     const float4* z = dp.zbuf + in.z_off;
     const int groups = dp.adj_groups;
-    float s = 0.f;
-    for (int g = 0; g < groups; ++g) {
-        const float4* zg = z + (size_t)g * w * w;
-        // cell (cx, cy) is stored at (cy + 1) * w + (cx + 1)
-        s += __ldg(&zg[(size_t)(py + 1) * w + px + 1].x) + __ldg(&zg[(size_t)(py + 1) * w + px].y) +
-             __ldg(&zg[(size_t)py * w + px + 1].z) + __ldg(&zg[(size_t)py * w + px].w);
-    }
+    // cell (cx, cy) is stored at (cy + 1) * w + (cx + 1)
+    const float s = corner_sum(z, (size_t)w * w, groups, (size_t)(py + 1) * w + px + 1, (size_t)(py + 1) * w + px,
+                               (size_t)py * w + px + 1, (size_t)py * w + px);
     const float val = s * in.inv_K;
     if constexpr (sizeof(T) == 4) fout[in.f_off + (size_t)py * n + px] = val;
     else fout[in.f_off + (size_t)py * n + px] = __float2bfloat16(val);

@@ -120,12 +120,8 @@ __global__ void __launch_bounds__(256) k_tv_update(DevPlan dp, const float* __re
         // A^T r at pixel (j, i): corner sums of cells (j,i), (j-1,i), (j,i-1), (j-1,i-1)
         const int w = n + 1;
         const float4* z = dp.zbuf + in.z_off;
-        float s = 0.f;
-        for (int g = 0; g < dp.adj_groups; ++g) {
-            const float4* zg = z + (size_t)g * w * w;
-            s += __ldg(&zg[(size_t)(i + 1) * w + j + 1].x) + __ldg(&zg[(size_t)(i + 1) * w + j].y) +
-                 __ldg(&zg[(size_t)i * w + j + 1].z) + __ldg(&zg[(size_t)i * w + j].w);
-        }
+        const float s = corner_sum(z, (size_t)w * w, dp.adj_groups, (size_t)(i + 1) * w + j + 1,
+                                   (size_t)(i + 1) * w + j, (size_t)i * w + j + 1, (size_t)i * w + j);
         const float adj = s * in.inv_K;
         const float eps2 = eps * eps;
         float dx, dy;
