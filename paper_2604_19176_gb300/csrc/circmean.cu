@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* 
             const int m = un.m0 + ml;
             const float mf = (float)m;
             const float4 d = __ldg(det + un.j);
-            const int Ui = __float2int_rz(floorf(d.x)), Vi = __float2int_rz(floorf(d.y));
+            const int Ui = __float2int_rz(d.x), Vi = __float2int_rz(d.y);
             const int base = (Vi + in.c0 - sg.band_lo) * W + Ui + in.c0 + CO;
             const int ul = ulo - Ui, vl = vlo - Vi;
             const float4* tq = rays_s + un.q0 + ql;   // units never wrap past K
@@ -224,7 +224,7 @@ __global__ void k_count_samples(DevPlan dp, int inst_idx, unsigned long long* __
     const InstDev in = dp.inst[inst_idx];
     const int j = blockIdx.x;
     const float4 d = dp.det[in.det_off + j];
-    const float Ui = floorf(d.x), Vi = floorf(d.y);
+    const float Ui = d.x, Vi = d.y;
     const float4* rays = dp.rays + in.ray_off;
     const float lo = (float)(-1 - in.c0), hi = (float)(in.n - 1 - in.c0);
     unsigned long long c = 0;

@@ -48,7 +48,7 @@ __device__ __forceinline__ void enumerate_cell(const DevPlan& dp, const InstDev&
     const int K = in.K;
     for (int j = j0; j < in.n_det; j += dj) {
         const float4 d = __ldg(det + j);
-        const float U = d.x, V = d.y;
+        const float U = d.x + d.z, V = d.y + d.w;   // approximate U, V for the candidate search
         const float du = ccx - U, dv = ccy - V;
         const float rc = sqrtf(fmaf(du, du, dv * dv));
         const int mlo = max(0, (int)ceilf((rc - kRcell) * in.inv_delta));
@@ -65,7 +65,7 @@ __device__ __forceinline__ void enumerate_cell(const DevPlan& dp, const InstDev&
         const float ax0 = (cxf - kSlabEps) - U, ax1 = (cxf + 1.f + kSlabEps) - U;
         const float ay0 = (cyf - kSlabEps) - V, ay1 = (cyf + 1.f + kSlabEps) - V;
         // the cell relative to the detector's integer part (exact: small integers)
-        const float cxr = cxf - floorf(U), cyr = cyf - floorf(V);
+        const float cxr = cxf - d.x, cyr = cyf - d.y;
         for (int i = 0; i < qn; ++i) {
             const int q = qlo + i;
             const float2 ri = __ldg(rtrig + q);
@@ -217,7 +217,7 @@ __device__ __forceinline__ void list_sample(const uint32_t code, int qb, int mbq
     const float w = __ldg(mb + j * n_rp + m);
     const float mf = (float)m;
     // the sample lies in this cell, so its relative cell is (cxf, cyf) - floor(U, V)
-    const float cxr = __fsub_rn(cxf, floorf(d.x)), cyr = __fsub_rn(cyf, floorf(d.y));
+    const float cxr = __fsub_rn(cxf, d.x), cyr = __fsub_rn(cyf, d.y);
     add_corners(z, cell_frac(mf, r.x, r.z, d.z, cxr), cell_frac(mf, r.y, r.w, d.w, cyr), w);
 }
 } // namespace

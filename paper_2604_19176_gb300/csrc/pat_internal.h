@@ -110,7 +110,7 @@ struct ImgTile {
 // Everything a kernel launch needs, by value (fits the 4 KB parameter space).
 struct DevPlan {
     const InstDev* inst;
-    const float4* det;             // (U, V, Uf, Vf) of each detector (split form), per instance
+    const float4* det;             // (Ui, Vi, Uf, Vf) of each detector (split form), per instance
     const float4* rays;            // (dcos hi, dsin hi, dcos lo, dsin lo) per q, 2K entries per instance
     const float2* rtrig;           // (1/dcos hi, 1/dsin hi), 2K entries per instance
     const float* P;                // Abel matrices P then P^T, per distinct n_t

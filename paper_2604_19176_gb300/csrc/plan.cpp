@@ -293,13 +293,14 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         d.p_off = p_off[g.n_t];
         d.det_off = (int32_t)detU.size();
         for (int j = 0; j < g.n_det; ++j) {
-            // split form: U (FP32), and the exact U minus floor(U) in FP32
+            // split form: Ui = floor(float(U)), and the exact U minus Ui in FP32
             const double th = g.arc_start + (j + 0.5) * g.arc_span / g.n_det;
             const double ue = std::cos(th) * (n / 2.0) - 0.5, ve = std::sin(th) * (n / 2.0) - 0.5;
             const float uf = (float)ue, vf = (float)ve;
             detU.push_back(uf);
             detV.push_back(vf);
-            det4.push_back(make_float4(uf, vf, (float)(ue - std::floor((double)uf)), (float)(ve - std::floor((double)vf))));
+            const double ui = std::floor((double)uf), vi = std::floor((double)vf);
+            det4.push_back(make_float4((float)ui, (float)vi, (float)(ue - ui), (float)(ve - vi)));
         }
         // reciprocal ray slopes for the adjoint's slab test, from the FP32 table values
         {
