@@ -232,6 +232,36 @@ pat_status_t pat_tv_step(pat_plan_t plan, const float* d_f_in, float* d_f_out, c
                          float lam, float eps, int32_t nonneg, float* d_delta, void* stream);
 
 /*
+ * pat_pdhg_step — one iteration of the primal-dual hybrid gradient method
+ * (Chambolle-Pock) for the TV problem of Eq. (4),
+ *     min_{f >= 0} 1/2 ||A f - g||^2 + alpha TV(f),
+ * the paper's TV baseline solver (Sec. 2.1).  TV is the unsmoothed isotropic
+ * total variation sum_i |grad f_i| with the forward differences of
+ * pat_tv_grad.  With K f = (A f, grad f), dual variables y (data shaped) and
+ * p = (px, py) (image shaped), one call performs, in this order:
+ *     px, py <- each (px_i, py_i) + sigma grad fbar_i projected onto the disk of radius alpha
+ *     y      <- (y + sigma (A fbar - g)) / (1 + sigma)
+ *     f_new  <- f - tau (A^T y + grad^T p), then max(f_new, 0) when nonneg != 0
+ *     fbar   <- 2 f_new - f;   f <- f_new
+ * Convergence needs sigma tau ||K||^2 < 1 with ||K||^2 <= ||A||^2 + 8.
+ * Start from f = fbar = y = px = py = 0 (or any warm start with fbar = f).
+ * FP32 plans only (PAT_ERR_UNSUPPORTED for BF16 plans).
+ *   d_f, d_fbar, d_px, d_py: device FP32 images (packed like pat_forward's
+ *            input), read and overwritten.
+ *   d_y:     device FP32 data-shaped dual variable, read and overwritten.
+ *   d_g:     device FP32 measured data (read only).
+ *   All six buffers 16-byte aligned, owned by the caller and pairwise
+ *   disjoint (PAT_ERR_INVALID_ARG otherwise).
+ *   sigma, tau: dual and primal steps, > 0.   alpha: TV weight, >= 0.
+ *   d_delta: nullable, two values per instance as in pat_descent_step
+ *            (||f_new - f||^2, ||f_new||^2), for the relative-change rule of
+ *            Sec. 2.3.
+ */
+pat_status_t pat_pdhg_step(pat_plan_t plan, float* d_f, float* d_fbar, float* d_y, float* d_px, float* d_py,
+                           const float* d_g, float sigma, float tau, float alpha, int32_t nonneg, float* d_delta,
+                           void* stream);
+
+/*
  * pat_plan_sync_status — synchronise the stream and report a device-side
  * error recorded by a bounded wait in a persistent launch (PAT_ERR_TIMEOUT),
  * clearing it.  Returns PAT_OK when none was recorded.
@@ -245,11 +275,13 @@ pat_status_t pat_plan_sync_status(pat_plan_t plan, void* stream);
  * per kernel kind into total_ms[kind] and launch counts into launches[kind]
  * (host arrays of n_kinds entries, either may be NULL) and forgets them.
  * Kinds (pat_kernel_kind_t order): circular means, Abel forward, Abel
- * adjoint, adjoint gather, TV, residual, descent step.
+ * adjoint, adjoint gather, TV, residual, descent step, fused TV update,
+ * primal-dual TV dual step, primal-dual primal step.
  */
 typedef enum {
     PAT_K_CIRCMEAN = 0, PAT_K_ABEL_FWD = 1, PAT_K_ABEL_ADJ = 2, PAT_K_ADJ_GATHER = 3,
-    PAT_K_TV = 4, PAT_K_RESIDUAL = 5, PAT_K_DESCENT = 6, PAT_K_TV_UPDATE = 7, PAT_K_COUNT = 8
+    PAT_K_TV = 4, PAT_K_RESIDUAL = 5, PAT_K_DESCENT = 6, PAT_K_TV_UPDATE = 7, PAT_K_PDHG_DUAL = 8,
+    PAT_K_PDHG_PRIMAL = 9, PAT_K_COUNT = 10
 } pat_kernel_kind_t;
 pat_status_t pat_plan_set_timing(pat_plan_t plan, int32_t enable);
 pat_status_t pat_plan_kernel_times(pat_plan_t plan, double* total_ms, int64_t* launches, int32_t n_kinds);

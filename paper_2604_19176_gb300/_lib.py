@@ -22,9 +22,11 @@ STATUS_NAMES = {
 EXPORTED = (
     "pat_plan_create", "pat_plan_destroy", "pat_plan_layout", "pat_plan_info", "pat_forward",
     "pat_adjoint", "pat_tv_grad", "pat_residual", "pat_descent_step", "pat_plan_sync_status",
-    "pat_plan_set_timing", "pat_plan_kernel_times", "pat_tv_grad_noalloc", "pat_tv_step", "pat_status_string",
+    "pat_plan_set_timing", "pat_plan_kernel_times", "pat_tv_grad_noalloc", "pat_tv_step", "pat_pdhg_step",
+    "pat_status_string",
 )
-KERNEL_KINDS = ("circmean", "abel_fwd", "abel_adj", "adjoint_gather", "tv", "residual", "descent", "tv_update")
+KERNEL_KINDS = ("circmean", "abel_fwd", "abel_adj", "adjoint_gather", "tv", "residual", "descent", "tv_update",
+                "pdhg_dual", "pdhg_primal")
 
 
 class PatGeometry(ctypes.Structure):
@@ -92,6 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pat_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i64p, i32]
     lib.pat_tv_grad_noalloc.argtypes = [vp, i32, i32, f32, vp, vp, vp]
     lib.pat_tv_step.argtypes = [vp, vp, vp, vp, f32, f32, f32, i32, vp, vp]
+    lib.pat_pdhg_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, f32, f32, f32, i32, vp, vp]
     lib.pat_status_string.argtypes = [i32]
     lib.pat_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:

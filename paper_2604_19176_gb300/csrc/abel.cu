@@ -47,11 +47,16 @@ struct AbelSmem {
 } // namespace
 
 // FWD: gin unused, gout = g (gsub nullable: gout = A f - gsub).
+// FWD && DUAL: gout = y (read and written), gsub = g:
+//   y <- (y + sigma (A f - g)) * inv1ps, the data-term dual step of the
+//   primal-dual iteration (the proximal map of the conjugate of
+//   1/2 ||. - g||^2), with inv1ps = 1 / (1 + sigma).
 // ADJ: gin = gbar, gout unused (writes Mbar in the plan workspace).
-template <bool FWD>
+template <bool FWD, bool DUAL>
 __global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel(DevPlan dp, const float* __restrict__ gin,
                                                              float* __restrict__ gout,
-                                                             const float* __restrict__ gsub, int cs)
+                                                             const float* __restrict__ gsub, int cs, float sigma,
+                                                             float inv1ps)
 {
     extern __shared__ __align__(16) unsigned char abel_smem[];
     AbelSmem& sm = *reinterpret_cast<AbelSmem*>(abel_smem);
@@ -159,7 +164,10 @@ __global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel(DevPlan dp, const f
                 if (j >= in.n_det) break;
                 const size_t o = in.g_off + (size_t)j * in.n_t + x;
                 const float v = r4[i] * in.inv_K;
-                gout[o] = gsub ? v - gsub[o] : v;
+                if (DUAL)
+                    gout[o] = fmaf(sigma, v - gsub[o], gout[o]) * inv1ps;
+                else
+                    gout[o] = gsub ? v - gsub[o] : v;
             }
         }
     } else {
@@ -175,22 +183,28 @@ __global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel(DevPlan dp, const f
 }
 
 namespace {
-template <bool FWD>
+template <bool FWD, bool DUAL = false>
 cudaError_t launch_abel(const DevPlan& dp, int tiles, int cs, const float* gin, float* gout, const float* gsub,
-                        cudaStream_t st)
+                        cudaStream_t st, float sigma = 0.f, float inv1ps = 1.f)
 {
     if (tiles == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_abel<FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_abel<FWD, DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(AbelSmem));
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_abel<FWD>, dim3((unsigned)(tiles * cs)), dim3(kAbelWarps * kWarp), sizeof(AbelSmem), st, cs,
-                      dp, gin, gout, gsub, cs);
+    return launch_pdl(k_abel<FWD, DUAL>, dim3((unsigned)(tiles * cs)), dim3(kAbelWarps * kWarp), sizeof(AbelSmem),
+                      st, cs, dp, gin, gout, gsub, cs, sigma, inv1ps);
 }
 } // namespace
 
 cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st, const float* gsub)
 {
     return launch_abel<true>(dp, dp.n_fwd_tiles, dp.abel_cluster_fwd, nullptr, g, gsub, st);
+}
+
+cudaError_t launch_abel_fwd_dual(const DevPlan& dp, float* y, const float* g, float sigma, float inv1ps,
+                                 cudaStream_t st)
+{
+    return launch_abel<true, true>(dp, dp.n_fwd_tiles, dp.abel_cluster_fwd, nullptr, y, g, st, sigma, inv1ps);
 }
 
 cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st)

@@ -302,6 +302,54 @@ pat_status_t pat_tv_step(pat_plan_t h, const float* d_f_in, float* d_f_out, cons
     return cuda_status(e);
 }
 
+namespace {
+// true when the byte ranges [a, a + na) and [b, b + nb) overlap
+bool overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+} // namespace
+
+pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, float* d_px, float* d_py,
+                           const float* d_g, float sigma, float tau, float alpha, int32_t nonneg, float* d_delta,
+                           void* stream)
+{
+    Plan* p = lookup(h);
+    if (!p) return PAT_ERR_BAD_PLAN;
+    if (p->dp.bf16) return PAT_ERR_UNSUPPORTED;
+    float* img[4] = {d_f, d_fbar, d_px, d_py};
+    for (float* q : img)
+        if (!q || !aligned16(q)) return PAT_ERR_INVALID_ARG;
+    if (!d_y || !d_g || !aligned16(d_y) || !aligned16(d_g)) return PAT_ERR_INVALID_ARG;
+    const size_t fb = sizeof(float) * (size_t)p->f_offsets.back(), gb = sizeof(float) * (size_t)p->g_offsets.back();
+    for (int a = 0; a < 4; ++a) {
+        for (int b = a + 1; b < 4; ++b)
+            if (overlap(img[a], fb, img[b], fb)) return PAT_ERR_INVALID_ARG;
+        if (overlap(img[a], fb, d_y, gb) || overlap(img[a], fb, d_g, gb)) return PAT_ERR_INVALID_ARG;
+    }
+    if (overlap(d_y, gb, d_g, gb)) return PAT_ERR_INVALID_ARG;
+    if (!(sigma > 0.f) || !std::isfinite(sigma) || !(tau > 0.f) || !std::isfinite(tau) || !(alpha >= 0.f) ||
+        !std::isfinite(alpha))
+        return PAT_ERR_INVALID_ARG;
+    DeviceScope ds(p->device);
+    if (!ds.ok) return PAT_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const DevPlan& dp = p->dp;
+    const float inv1ps = 1.f / (1.f + sigma);
+    cudaError_t e = timed(*p, PAT_K_PDHG_DUAL, st,
+                          [&] { return launch_pdhg_dual_tv(dp, d_fbar, d_px, d_py, sigma, alpha, st); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return launch_circmean(dp, d_fbar, st); });
+    if (e == cudaSuccess)
+        e = timed(*p, PAT_K_ABEL_FWD, st, [&] { return launch_abel_fwd_dual(dp, d_y, d_g, sigma, inv1ps, st); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, d_y, st); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return launch_adjoint_cells(dp, st); });
+    if (e == cudaSuccess)
+        e = timed(*p, PAT_K_PDHG_PRIMAL, st,
+                  [&] { return launch_pdhg_primal(dp, d_f, d_fbar, d_px, d_py, tau, nonneg, d_delta, st); });
+    return cuda_status(e);
+}
+
 pat_status_t pat_plan_sync_status(pat_plan_t h, void* stream)
 {
     Plan* p = lookup(h);

@@ -154,6 +154,102 @@ __global__ void __launch_bounds__(256) k_tv_update(DevPlan dp, const float* __re
     }
 }
 
+// Primal-dual (Chambolle-Pock) TV iteration for Eq. (4), written as
+// min_f F(K f) + G(f) with K f = (A f, grad f), F(z, q) = 1/2 ||z - g||^2 +
+// alpha sum_i |q_i| and G the indicator of f >= 0.  The dual variable of the
+// TV term is p = (px, py), one 2-vector per pixel, stored as two image-shaped
+// planes.  grad is the forward difference of k_tv (zero on the last column /
+// row) and grad^T its exact transpose.
+//
+// Dual step of the TV term: p <- projection onto |p_i| <= alpha of
+// p + sigma grad fbar, pixel by pixel, in place.
+__global__ void __launch_bounds__(256) k_pdhg_dual_tv(DevPlan dp, const float* __restrict__ fbar,
+                                                      float* __restrict__ px, float* __restrict__ py, float sigma,
+                                                      float alpha)
+{
+    const ImgTile t = dp.img_tiles[blockIdx.x];
+    const InstDev in = dp.inst[t.inst];
+    pdl_wait();   // fbar and p come from the previous iteration
+    const int n = in.n;
+    const int j = t.x0 + (threadIdx.x & 31), i = t.y0 + (threadIdx.x >> 5);
+    if (i >= n || j >= n) return;
+    const float* fi = fbar + in.f_off;
+    const size_t idx = in.f_off + (size_t)i * n + j;
+    const float c = fi[(size_t)i * n + j];
+    const float dx = (j + 1 < n) ? fi[(size_t)i * n + j + 1] - c : 0.f;
+    const float dy = (i + 1 < n) ? fi[(size_t)(i + 1) * n + j] - c : 0.f;
+    const float qx = fmaf(sigma, dx, px[idx]);
+    const float qy = fmaf(sigma, dy, py[idx]);
+    const float mag = sqrtf(fmaf(qx, qx, qy * qy));
+    const float s = mag > alpha ? alpha / mag : 1.f;
+    px[idx] = qx * s;
+    py[idx] = qy * s;
+}
+
+// Primal step and extrapolation, in place:
+//   f_new = max(0, f - tau (A^T y + grad^T p)),  fbar = 2 f_new - f,  f = f_new
+// with A^T y from the four cells' corner sums (as k_adj_combine), and the
+// per-tile sums of |f_new - f|^2 and |f_new|^2 for the relative-change rule.
+__global__ void __launch_bounds__(256) k_pdhg_primal(DevPlan dp, float* __restrict__ f, float* __restrict__ fbar,
+                                                     const float* __restrict__ px, const float* __restrict__ py,
+                                                     float tau, int nonneg, float* __restrict__ part)
+{
+    __shared__ float red[8];
+    const ImgTile t = dp.img_tiles[blockIdx.x];
+    const InstDev in = dp.inst[t.inst];
+    pdl_wait();   // the cell sums come from the previous kernel
+    const int n = in.n;
+    const int j = t.x0 + (threadIdx.x & 31), i = t.y0 + (threadIdx.x >> 5);
+    float d2 = 0.f, n2 = 0.f;
+    if (i < n && j < n) {
+        const int w = n + 1;
+        const float4* z = dp.zbuf + in.z_off;
+        const float s = corner_sum(z, (size_t)w * w, dp.adj_groups, (size_t)(i + 1) * w + j + 1,
+                                   (size_t)(i + 1) * w + j, (size_t)i * w + j + 1, (size_t)i * w + j);
+        const size_t idx = in.f_off + (size_t)i * n + j;
+        // grad^T p: the differences that pixel (j, i) enters with +1 (from the
+        // left / upper neighbour) and -1 (its own, unless on the last column / row)
+        float div = 0.f;
+        if (j > 0) div += px[idx - 1];
+        if (j + 1 < n) div -= px[idx];
+        if (i > 0) div += py[idx - n];
+        if (i + 1 < n) div -= py[idx];
+        const float old = f[idx];
+        float nv = fmaf(-tau, fmaf(s, in.inv_K, div), old);
+        if (nonneg) nv = fmaxf(nv, 0.f);
+        f[idx] = nv;
+        fbar[idx] = fmaf(2.f, nv, -old);
+        d2 = (nv - old) * (nv - old);
+        n2 = nv * nv;
+    }
+    if (part) {
+        const float s0 = block_sum<256>(d2, red);
+        const float s1 = block_sum<256>(n2, red);
+        if (threadIdx.x == 0) {
+            part[2 * blockIdx.x] = s0;
+            part[2 * blockIdx.x + 1] = s1;
+        }
+    }
+}
+
+cudaError_t launch_pdhg_dual_tv(const DevPlan& dp, const float* fbar, float* px, float* py, float sigma, float alpha,
+                                cudaStream_t st)
+{
+    if (dp.n_img_tiles == 0) return cudaSuccess;
+    return launch_pdl(k_pdhg_dual_tv, dim3(dp.n_img_tiles), dim3(256), 0, st, 1, dp, fbar, px, py, sigma, alpha);
+}
+
+cudaError_t launch_pdhg_primal(const DevPlan& dp, float* f, float* fbar, const float* px, const float* py, float tau,
+                               int nonneg, float* delta, cudaStream_t st)
+{
+    if (dp.n_img_tiles == 0) return cudaSuccess;
+    cudaError_t e = launch_pdl(k_pdhg_primal, dim3(dp.n_img_tiles), dim3(256), 0, st, 1, dp, f, fbar, px, py, tau,
+                               nonneg, delta ? dp.tv_partial : nullptr);
+    if (e != cudaSuccess || !delta) return e;
+    k_tile_sums<<<dp.n_inst, 32, 0, st>>>(dp, dp.tv_partial, 2, delta);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tv_update(const DevPlan& dp, const float* f_in, float* f_out, float tau, float lam, float eps,
                              int nonneg, float* delta, cudaStream_t st)
 {

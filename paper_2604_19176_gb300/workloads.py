@@ -93,4 +93,14 @@ def vessel1024_b8() -> Workload:
                      "seeds": list(range(5, 13))})
 
 
-ALL = {w.__name__: w for w in (gauss64_full, vessel256_half, vessel512_half, batch64_uneven, vessel1024_b8)}
+def exp760_270() -> Workload:
+    """The experimental-data geometry of Sec. 2.4.2: a 760x760 image, 256
+    detectors on 270 degrees and 2030 time samples, with a synthetic phantom
+    (12 tubes + 5 Gaussians) standing in for the measured one; K = 2N."""
+    return Workload("exp760_270", (_arc(760, 256, 270.0, 2030, 1520),),
+                    "N=760, 12 vessel tubes + 5 Gaussians (seed 9), 256 detectors / 270 deg, n_t=2030, T=2, K=1520",
+                    {"phantom": "mixed", "tubes": 12, "gaussians": 5, "seeds": [9]})
+
+
+ALL = {w.__name__: w for w in (gauss64_full, vessel256_half, vessel512_half, batch64_uneven, vessel1024_b8,
+                               exp760_270)}
