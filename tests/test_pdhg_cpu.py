@@ -63,10 +63,12 @@ def _problem(n, m, seed):
     return A, g
 
 
-def _run(A, g, n, alpha, iters, nonneg=True):
+def _run(A, g, n, alpha, iters, nonneg=True, mean_penalty=None, tau=None):
     L = math.sqrt(np.linalg.norm(A, 2) ** 2 + 8.0)
-    st, rel = P.pdhg(lambda f: A @ f.ravel(), lambda y: (A.T @ y).reshape(n, n), g, n, alpha, 0.99 / L, 0.99 / L,
-                     iters, nonneg=nonneg)
+    tau = 0.99 / L if tau is None else tau
+    sigma = 0.98 / (tau * L * L)
+    st, rel = P.pdhg(lambda f: A @ f.ravel(), lambda y: (A.T @ y).reshape(n, n), g, n, alpha, sigma, tau,
+                     iters, nonneg=nonneg, mean_penalty=mean_penalty)
     return st, rel
 
 
@@ -86,6 +88,23 @@ def test_alpha_zero_without_constraint_is_least_squares():
     st, _ = _run(A, g, n, 0.0, 6000, nonneg=False)
     ref = np.linalg.lstsq(A, g, rcond=None)[0]
     assert np.max(np.abs(st["f"].ravel() - ref)) < 1e-8
+
+
+@pytest.mark.parametrize("beta,c,tau", [(3.0, 0.4, None), (100.0, -0.2, 0.006)])
+def test_mean_penalty_is_augmented_least_squares(beta, c, tau):
+    """alpha = 0, no constraint, penalty beta/2 (mean f - c)^2: the minimiser is
+    the least-squares solution of [A; sqrt(beta) 1^T / P] f = [g; sqrt(beta) c].
+    The larger beta needs the smaller tau: 1/tau - sigma ||K||^2 >= beta / (2 P)."""
+    n = 4
+    A, g = _problem(n, 40, seed=12)
+    P_ = n * n
+    Aa = np.vstack([A, math.sqrt(beta) * np.ones((1, P_)) / P_])
+    ref = np.linalg.lstsq(Aa, np.concatenate([g, [math.sqrt(beta) * c]]), rcond=None)[0]
+    st, _ = _run(A, g, n, 0.0, 20000, nonneg=False, mean_penalty=(beta, c), tau=tau)
+    assert np.max(np.abs(st["f"].ravel() - ref)) < 1e-8
+    # the penalty moved the mean towards c
+    free = np.linalg.lstsq(A, g, rcond=None)[0]
+    assert abs(ref.mean() - c) < abs(free.mean() - c)
 
 
 def test_large_alpha_gives_best_constant_image():
