@@ -241,10 +241,16 @@ pat_status_t pat_tv_step(pat_plan_t plan, const float* d_f_in, float* d_f_out, c
  * p = (px, py) (image shaped), one call performs, in this order:
  *     px, py <- each (px_i, py_i) + sigma grad fbar_i projected onto the disk of radius alpha
  *     y      <- (y + sigma (A fbar - g)) / (1 + sigma)
- *     f_new  <- f - tau (A^T y + grad^T p), then max(f_new, 0) when nonneg != 0
+ *     f_new  <- f - tau (A^T y + grad^T p + beta (mean(f) - c) / P),
+ *               then max(f_new, 0) when nonneg != 0
  *     fbar   <- 2 f_new - f;   f <- f_new
  * Convergence needs sigma tau ||K||^2 < 1 with ||K||^2 <= ||A||^2 + 8.
  * Start from f = fbar = y = px = py = 0 (or any warm start with fbar = f).
+ * The beta term is the mouse-data variant of Sec. 2.1: with nonneg = 0 and
+ * beta > 0 the objective gains the quadratic mean-intensity penalty
+ * beta/2 (mean(f) - c)^2 (P pixels per instance), taken as an explicit
+ * gradient step (primal-dual method with a smooth term; it also needs
+ * 1/tau - sigma ||K||^2 >= beta / (2 P)).
  * FP32 plans only (PAT_ERR_UNSUPPORTED for BF16 plans).
  *   d_f, d_fbar, d_px, d_py: device FP32 images (packed like pat_forward's
  *            input), read and overwritten.
@@ -253,13 +259,18 @@ pat_status_t pat_tv_step(pat_plan_t plan, const float* d_f_in, float* d_f_out, c
  *   All six buffers 16-byte aligned, owned by the caller and pairwise
  *   disjoint (PAT_ERR_INVALID_ARG otherwise).
  *   sigma, tau: dual and primal steps, > 0.   alpha: TV weight, >= 0.
+ *   beta:    mean-penalty weight, >= 0 (0: no penalty).   mean_target: c.
+ *   d_fmean: device FP32, one value per instance, disjoint from the others;
+ *            read as the mean of f on entry, overwritten with the mean of
+ *            f_new.  Required when beta > 0 (initialise it with the mean of
+ *            the starting f), else nullable.
  *   d_delta: nullable, two values per instance as in pat_descent_step
  *            (||f_new - f||^2, ||f_new||^2), for the relative-change rule of
  *            Sec. 2.3.
  */
 pat_status_t pat_pdhg_step(pat_plan_t plan, float* d_f, float* d_fbar, float* d_y, float* d_px, float* d_py,
-                           const float* d_g, float sigma, float tau, float alpha, int32_t nonneg, float* d_delta,
-                           void* stream);
+                           const float* d_g, float sigma, float tau, float alpha, int32_t nonneg, float beta,
+                           float mean_target, float* d_fmean, float* d_delta, void* stream);
 
 /*
  * pat_plan_sync_status — synchronise the stream and report a device-side

@@ -94,7 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pat_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i64p, i32]
     lib.pat_tv_grad_noalloc.argtypes = [vp, i32, i32, f32, vp, vp, vp]
     lib.pat_tv_step.argtypes = [vp, vp, vp, vp, f32, f32, f32, i32, vp, vp]
-    lib.pat_pdhg_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, f32, f32, f32, i32, vp, vp]
+    lib.pat_pdhg_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, f32, f32, f32, i32, f32, f32, vp, vp, vp]
     lib.pat_status_string.argtypes = [i32]
     lib.pat_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:

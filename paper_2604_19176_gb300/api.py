@@ -239,20 +239,24 @@ class PatPlan:
 
     def pdhg_step(self, f: torch.Tensor, fbar: torch.Tensor, y: torch.Tensor, px: torch.Tensor, py: torch.Tensor,
                   g: torch.Tensor, sigma: float, tau: float, alpha: float, nonneg: bool = True,
-                  delta: torch.Tensor | None = None, stream=None) -> None:
+                  delta: torch.Tensor | None = None, beta: float = 0.0, mean_target: float = 0.0,
+                  fmean: torch.Tensor | None = None, stream=None) -> None:
         """One primal-dual (Chambolle-Pock) TV iteration for Eq. (4), in place on
-        f, fbar, y, px, py (see ``pat_pdhg_step``)."""
+        f, fbar, y, px, py (and fmean); ``beta`` > 0 adds the mean-intensity
+        penalty beta/2 (mean f - mean_target)^2 (see ``pat_pdhg_step``)."""
         for t, name in ((f, "f"), (fbar, "fbar"), (px, "px"), (py, "py")):
             self._check(t, self.f_elems, torch.float32, name)
         self._check(y, self.g_elems, torch.float32, "y")
         self._check(g, self.g_elems, torch.float32, "g")
         if delta is not None:
             self._check(delta, 2 * len(self.geoms), torch.float32, "delta")
-        ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        if fmean is not None:
+            self._check(fmean, len(self.geoms), torch.float32, "fmean")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)  # noqa: E731
         _lib.check("pat_pdhg_step", self._lib.pat_pdhg_step(
             self._h, ptr(f), ptr(fbar), ptr(y), ptr(px), ptr(py), ptr(g), ctypes.c_float(sigma), ctypes.c_float(tau),
-            ctypes.c_float(alpha), 1 if nonneg else 0, ctypes.c_void_p(delta.data_ptr() if delta is not None else 0),
-            _stream_ptr(stream, self.device)))
+            ctypes.c_float(alpha), 1 if nonneg else 0, ctypes.c_float(beta), ctypes.c_float(mean_target), ptr(fmean),
+            ptr(delta), _stream_ptr(stream, self.device)))
 
     def set_timing(self, enable: bool) -> None:
         """Bracket every kernel launch of this plan with CUDA events."""

@@ -312,8 +312,8 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb)
 } // namespace
 
 pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, float* d_px, float* d_py,
-                           const float* d_g, float sigma, float tau, float alpha, int32_t nonneg, float* d_delta,
-                           void* stream)
+                           const float* d_g, float sigma, float tau, float alpha, int32_t nonneg, float beta,
+                           float mean_target, float* d_fmean, float* d_delta, void* stream)
 {
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
@@ -330,8 +330,17 @@ pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, 
     }
     if (overlap(d_y, gb, d_g, gb)) return PAT_ERR_INVALID_ARG;
     if (!(sigma > 0.f) || !std::isfinite(sigma) || !(tau > 0.f) || !std::isfinite(tau) || !(alpha >= 0.f) ||
-        !std::isfinite(alpha))
+        !std::isfinite(alpha) || !(beta >= 0.f) || !std::isfinite(beta) || !std::isfinite(mean_target))
         return PAT_ERR_INVALID_ARG;
+    if (beta > 0.f && !d_fmean) return PAT_ERR_INVALID_ARG;
+    if (d_fmean) {
+        const size_t mb = sizeof(float) * (size_t)p->n_inst;
+        if (reinterpret_cast<uintptr_t>(d_fmean) & 3u) return PAT_ERR_INVALID_ARG;
+        for (float* q : img)
+            if (overlap(q, fb, d_fmean, mb)) return PAT_ERR_INVALID_ARG;
+        if (overlap(d_y, gb, d_fmean, mb) || overlap(d_g, gb, d_fmean, mb)) return PAT_ERR_INVALID_ARG;
+        if (d_delta && overlap(d_delta, 2 * mb, d_fmean, mb)) return PAT_ERR_INVALID_ARG;
+    }
     DeviceScope ds(p->device);
     if (!ds.ok) return PAT_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -346,7 +355,10 @@ pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, 
     if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return launch_adjoint_cells(dp, st); });
     if (e == cudaSuccess)
         e = timed(*p, PAT_K_PDHG_PRIMAL, st,
-                  [&] { return launch_pdhg_primal(dp, d_f, d_fbar, d_px, d_py, tau, nonneg, d_delta, st); });
+                  [&] {
+                      return launch_pdhg_primal(dp, d_f, d_fbar, d_px, d_py, tau, nonneg, d_fmean, beta, mean_target,
+                                                d_delta, st);
+                  });
     return cuda_status(e);
 }
 

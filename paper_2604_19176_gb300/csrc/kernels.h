@@ -52,11 +52,13 @@ cudaError_t launch_tv_update(const DevPlan& dp, const float* f_in, float* f_out,
 // Primal-dual TV iteration (Eq. (4)): dual step of the TV term, in place,
 // p <- proj_{|p_i| <= alpha}(p + sigma grad fbar); and the primal step with
 // extrapolation from the adjoint cell sums, f <- max(0, f - tau (A^T y +
-// grad^T p)), fbar <- 2 f_new - f_old; delta as pat_descent_step.
+// grad^T p + beta (mean f - c) / P)), fbar <- 2 f_new - f_old; delta as
+// pat_descent_step; fmean (nullable, per instance) read as the mean of f and
+// overwritten with the mean of f_new (the penalty term needs it).
 cudaError_t launch_pdhg_dual_tv(const DevPlan& dp, const float* fbar, float* px, float* py, float sigma, float alpha,
                                 cudaStream_t st);
 cudaError_t launch_pdhg_primal(const DevPlan& dp, float* f, float* fbar, const float* px, const float* py, float tau,
-                               int nonneg, float* delta, cudaStream_t st);
+                               int nonneg, float* fmean, float beta, float mean_target, float* delta, cudaStream_t st);
 // Time stage of A with the data-term dual step of the primal-dual iteration
 // as its epilogue: y <- (y + sigma (A fbar - g)) * inv1ps, inv1ps = 1/(1+sigma).
 cudaError_t launch_abel_fwd_dual(const DevPlan& dp, float* y, const float* g, float sigma, float inv1ps,

@@ -187,12 +187,16 @@ __global__ void __launch_bounds__(256) k_pdhg_dual_tv(DevPlan dp, const float* _
 }
 
 // Primal step and extrapolation, in place:
-//   f_new = max(0, f - tau (A^T y + grad^T p)),  fbar = 2 f_new - f,  f = f_new
+//   f_new = max(0, f - tau (A^T y + grad^T p + grad h(f))),  fbar = 2 f_new - f,  f = f_new
 // with A^T y from the four cells' corner sums (as k_adj_combine), and the
-// per-tile sums of |f_new - f|^2 and |f_new|^2 for the relative-change rule.
+// per-tile sums of |f_new - f|^2, |f_new|^2 and f_new for the relative-change
+// rule and the instance mean.  h(f) = beta/2 (mean(f) - c)^2 is the optional
+// mean-intensity penalty (beta != 0; fmean then holds the mean of f per
+// instance), an explicit gradient term beta (mean(f) - c) / P on every pixel.
 __global__ void __launch_bounds__(256) k_pdhg_primal(DevPlan dp, float* __restrict__ f, float* __restrict__ fbar,
                                                      const float* __restrict__ px, const float* __restrict__ py,
-                                                     float tau, int nonneg, float* __restrict__ part)
+                                                     float tau, int nonneg, const float* __restrict__ fmean,
+                                                     float beta, float mean_target, float* __restrict__ part)
 {
     __shared__ float red[8];
     const ImgTile t = dp.img_tiles[blockIdx.x];
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(256) k_pdhg_primal(DevPlan dp, float* __restri
     pdl_wait();   // the cell sums come from the previous kernel
     const int n = in.n;
     const int j = t.x0 + (threadIdx.x & 31), i = t.y0 + (threadIdx.x >> 5);
-    float d2 = 0.f, n2 = 0.f;
+    float d2 = 0.f, n2 = 0.f, s1 = 0.f;
     if (i < n && j < n) {
         const int w = n + 1;
         const float4* z = dp.zbuf + in.z_off;
@@ -214,6 +218,7 @@ __global__ void __launch_bounds__(256) k_pdhg_primal(DevPlan dp, float* __restri
         if (j + 1 < n) div -= px[idx];
         if (i > 0) div += py[idx - n];
         if (i + 1 < n) div -= py[idx];
+        if (beta != 0.f) div += beta * (fmean[t.inst] - mean_target) / ((float)n * (float)n);
         const float old = f[idx];
         float nv = fmaf(-tau, fmaf(s, in.inv_K, div), old);
         if (nonneg) nv = fmaxf(nv, 0.f);
@@ -221,14 +226,35 @@ __global__ void __launch_bounds__(256) k_pdhg_primal(DevPlan dp, float* __restri
         fbar[idx] = fmaf(2.f, nv, -old);
         d2 = (nv - old) * (nv - old);
         n2 = nv * nv;
+        s1 = nv;
     }
     if (part) {
-        const float s0 = block_sum<256>(d2, red);
-        const float s1 = block_sum<256>(n2, red);
+        const float a = block_sum<256>(d2, red);
+        const float b = block_sum<256>(n2, red);
+        const float c = block_sum<256>(s1, red);
         if (threadIdx.x == 0) {
-            part[2 * blockIdx.x] = s0;
-            part[2 * blockIdx.x + 1] = s1;
+            part[3 * blockIdx.x] = a;
+            part[3 * blockIdx.x + 1] = b;
+            part[3 * blockIdx.x + 2] = c;
         }
+    }
+}
+
+// Per-instance sums of k_pdhg_primal's partials (fixed order): delta[2i],
+// delta[2i+1] = |f_new - f|^2, |f_new|^2 and fmean[i] = mean of f_new (each nullable).
+__global__ void k_pdhg_sums(DevPlan dp, const float* __restrict__ part, float* __restrict__ delta,
+                            float* __restrict__ fmean)
+{
+    const int inst = blockIdx.x, c = threadIdx.x;
+    if (c >= 3) return;
+    float s = 0.f;
+    for (int b = 0; b < dp.n_img_tiles; ++b)
+        if (dp.img_tiles[b].inst == inst) s += part[(size_t)b * 3 + c];
+    if (c < 2) {
+        if (delta) delta[2 * inst + c] = s;
+    } else if (fmean) {
+        const int n = dp.inst[inst].n;
+        fmean[inst] = s / ((float)n * (float)n);
     }
 }
 
@@ -240,13 +266,14 @@ cudaError_t launch_pdhg_dual_tv(const DevPlan& dp, const float* fbar, float* px,
 }
 
 cudaError_t launch_pdhg_primal(const DevPlan& dp, float* f, float* fbar, const float* px, const float* py, float tau,
-                               int nonneg, float* delta, cudaStream_t st)
+                               int nonneg, float* fmean, float beta, float mean_target, float* delta, cudaStream_t st)
 {
     if (dp.n_img_tiles == 0) return cudaSuccess;
+    const bool sums = delta || fmean;
     cudaError_t e = launch_pdl(k_pdhg_primal, dim3(dp.n_img_tiles), dim3(256), 0, st, 1, dp, f, fbar, px, py, tau,
-                               nonneg, delta ? dp.tv_partial : nullptr);
-    if (e != cudaSuccess || !delta) return e;
-    k_tile_sums<<<dp.n_inst, 32, 0, st>>>(dp, dp.tv_partial, 2, delta);
+                               nonneg, (const float*)fmean, beta, mean_target, sums ? dp.tv_partial : nullptr);
+    if (e != cudaSuccess || !sums) return e;
+    k_pdhg_sums<<<dp.n_inst, 32, 0, st>>>(dp, dp.tv_partial, delta, fmean);
     return cudaGetLastError();
 }
 

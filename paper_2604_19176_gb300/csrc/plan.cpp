@@ -670,7 +670,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
 
     // workspace (floats): forward slots | Mbar | TV partials | (aligned) cell sums (float4)
     // workspace (4-byte words): slots | M | Mbar | TV partials | arrival counters | cell sums (float4)
-    const int64_t tv_parts = 2 * (int64_t)itiles.size();
+    const int64_t tv_parts = 3 * (int64_t)itiles.size();
     const int64_t o_msum = mpart_total, o_mbar = o_msum + mbar_total, o_tvp = o_mbar + mbar_total;
     const int64_t o_arr = o_tvp + tv_parts;
     const int64_t o_ctr = ((o_arr + arrive_total + kQueueStride - 1) / kQueueStride) * kQueueStride;

@@ -163,29 +163,40 @@ def tv_reconstruct(plan: PatPlan, g: torch.Tensor, alpha: float, eps: float = 1e
     return f, hist
 
 
-def pdhg_steps(plan: PatPlan, g: torch.Tensor, alpha: float) -> tuple:
-    """Step sizes sigma = tau = 0.99 / ||K|| for the primal-dual iteration, with
-    ||K||^2 <= ||A||^2 + 8 (||grad||^2 <= 8 for forward differences)."""
-    s = 0.99 / math.sqrt(operator_norm_sq(plan) + 8.0)
-    return s, s
+def pdhg_steps(plan: PatPlan, beta: float = 0.0) -> tuple:
+    """Step sizes (sigma, tau) for the primal-dual iteration: sigma = tau =
+    0.99 / ||K|| with ||K||^2 <= ||A||^2 + 8 (||grad||^2 <= 8 for forward
+    differences).  With the mean penalty (beta > 0, gradient Lipschitz constant
+    beta / P) tau is lowered until 1/tau - sigma ||K||^2 >= beta / (2 P), with
+    sigma tau ||K||^2 = 0.98 kept."""
+    k2 = operator_norm_sq(plan) + 8.0
+    tau = 0.99 / math.sqrt(k2)
+    if beta > 0:
+        p_min = min(g.n * g.n for g in plan.geoms)
+        tau = min(tau, 0.02 * 2.0 * p_min / beta)
+    return 0.98 / (tau * k2), tau
 
 
 @torch.no_grad()
 def pdhg_reconstruct(plan: PatPlan, g: torch.Tensor, alpha: float, iters: int = 1000,
                      sigma: Optional[float] = None, tau: Optional[float] = None, nonneg: bool = True,
-                     stop_tol: float = 1e-4, check_every: int = 1, state: Optional[dict] = None,
-                     callback: Optional[Callable] = None) -> tuple:
+                     mean_penalty: Optional[tuple] = None, stop_tol: float = 1e-4, check_every: int = 1,
+                     state: Optional[dict] = None, callback: Optional[Callable] = None) -> tuple:
     """Primal-dual hybrid gradient (Chambolle-Pock) for Eq. (4):
     min_{f >= 0} 1/2 ||A f - g||^2 + alpha TV(f), the paper's TV baseline
     solver (Sec. 2.1); each iteration is one ``pat_pdhg_step``.
 
+    The mouse-data variant (Sec. 2.1) is ``nonneg=False`` with
+    ``mean_penalty=(beta, c)``: + beta/2 (mean(f) - c)^2 per instance.
     Stops when ||f_k - f_{k-1}|| / ||f_k|| <= stop_tol for every instance
     (Sec. 2.3), tested every ``check_every`` iterations (the test reads two
-    numbers per instance back to the host).  ``state`` (f, fbar, y, px, py)
-    resumes a run.  Returns (f, history of (iteration, max relative change), state).
+    numbers per instance back to the host).  ``state`` (f, fbar, y, px, py,
+    and fmean with the penalty) resumes a run.  Returns (f, history of
+    (iteration, max relative change), state).
     """
+    beta, c = mean_penalty if mean_penalty is not None else (0.0, 0.0)
     if sigma is None or tau is None:
-        s0, t0 = pdhg_steps(plan, g, alpha)
+        s0, t0 = pdhg_steps(plan, beta)
         sigma = s0 if sigma is None else sigma
         tau = t0 if tau is None else tau
     dev = plan.device
@@ -193,12 +204,17 @@ def pdhg_reconstruct(plan: PatPlan, g: torch.Tensor, alpha: float, iters: int = 
         z = lambda shape: torch.zeros(shape, dtype=torch.float32, device=dev)  # noqa: E731
         state = {"f": z(plan.image_shape()), "fbar": z(plan.image_shape()), "y": z(plan.data_shape()),
                  "px": z(plan.image_shape()), "py": z(plan.image_shape())}
+    if beta > 0 and "fmean" not in state:
+        fo = plan.layout()[0]
+        flat = state["f"].reshape(-1)
+        state["fmean"] = torch.stack([flat[fo[i]:fo[i + 1]].mean() for i in range(len(plan.geoms))]).float()
     delta = torch.empty(2 * len(plan.geoms), dtype=torch.float32, device=dev)
     hist = []
     for k in range(iters):
         check = (k + 1) % check_every == 0 or k + 1 == iters
         plan.pdhg_step(state["f"], state["fbar"], state["y"], state["px"], state["py"], g, sigma, tau, alpha,
-                       nonneg=nonneg, delta=delta if check else None)
+                       nonneg=nonneg, delta=delta if check else None, beta=beta, mean_target=c,
+                       fmean=state.get("fmean") if beta > 0 else None)
         if check:
             d = delta.view(-1, 2)
             r = float(torch.sqrt(d[:, 0] / torch.clamp(d[:, 1], min=1e-30)).max())
@@ -213,12 +229,15 @@ def pdhg_reconstruct(plan: PatPlan, g: torch.Tensor, alpha: float, iters: int = 
 def dip_reconstruct(plan: PatPlan, g: torch.Tensor, z: torch.Tensor, lam: float = 1e-4, eps: float = 1e-3,
                     steps: int = 2000, lr: float = 1e-4, cosine: bool = False, net: Optional[nn.Module] = None,
                     checkpoint: Optional[str] = None, checkpoint_every: int = 100,
-                    callback: Optional[Callable] = None, seed: int = 0) -> tuple:
+                    callback: Optional[Callable] = None, seed: int = 0,
+                    mean_penalty: Optional[tuple] = None) -> tuple:
     """DIP of Eq. (5): theta* = argmin ||A phi_theta(z) - g||^2 + lam TV(phi_theta(z)).
 
     Adam at ``lr`` (cosine annealing over all steps if ``cosine``).  With
     ``checkpoint`` set, network/optimiser state and the step counter are saved
     every ``checkpoint_every`` steps and resumed from if the file exists.
+    ``mean_penalty=(beta, c)`` adds beta (mean(f) - c)^2, the mean-intensity
+    term of the mouse-data variant (Sec. 2.2; use with ``UNet(mouse=True)``).
     Returns (f = phi_theta(z), loss history).
     """
     dev = plan.device
@@ -242,6 +261,8 @@ def dip_reconstruct(plan: PatPlan, g: torch.Tensor, z: torch.Tensor, lam: float 
         f = net(z).reshape(img_shape)
         r = pat_apply(f, plan) - g
         loss = (r * r).sum() + lam * tv_value(f, plan, eps).sum()
+        if mean_penalty is not None:
+            loss = loss + mean_penalty[0] * (f.mean() - mean_penalty[1]) ** 2
         loss.backward()
         opt.step()
         if sched is not None:

@@ -65,3 +65,7 @@ def test_host_validation_without_gpu(lib):
     assert lib.pat_tv_grad(None, None, ctypes.c_float(1e-3), None, None, None) == 6
     assert lib.pat_plan_destroy(None) == 6
     assert lib.pat_plan_info(None, None) == 6
+    f = ctypes.c_float
+    assert lib.pat_pdhg_step(None, None, None, None, None, None, None, f(0.1), f(0.1), f(1e-3), 1, f(0.0), f(0.0),
+                             None, None, None) == 6
+    assert lib.pat_tv_step(None, None, None, None, f(0.1), f(1e-3), f(1e-3), 1, None, None) == 6

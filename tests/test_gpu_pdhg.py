@@ -56,8 +56,10 @@ def _gpu_state(plan, dev):
             "px": z(plan.image_shape()), "py": z(plan.image_shape())}
 
 
-@pytest.mark.parametrize("nonneg", [True, False])
-def test_pdhg_iterates_match_oracle(cuda_dev, nonneg):
+@pytest.mark.parametrize("nonneg,beta", [(True, 0.0), (False, 0.0), (False, 200.0)])
+def test_pdhg_iterates_match_oracle(cuda_dev, nonneg, beta):
+    """beta > 0 is the mouse-data variant: no f >= 0, mean-intensity penalty
+    beta/2 (mean f - 0.2)^2."""
     g = Geometry(64, 48, 0.3, 1.5 * math.pi, 96, 2.0, 128)
     data = _data(g, seed=5)
     s = 0.99 / math.sqrt(_oracle_norm_sq(g) + 8.0)
@@ -66,13 +68,18 @@ def test_pdhg_iterates_match_oracle(cuda_dev, nonneg):
     st = _gpu_state(plan, cuda_dev)
     gd = torch.tensor(data, dtype=torch.float32, device=cuda_dev)
     delta = torch.zeros(2, device=cuda_dev)
+    fmean = torch.zeros(1, device=cuda_dev)
     ost = None
     A = lambda f: O.forward(og(g), f)  # noqa: E731
     At = lambda y: O.adjoint(og(g), y)  # noqa: E731
+    mp = (beta, 0.2) if beta > 0 else None
     for k in range(12):
-        plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, s, s, alpha, nonneg=nonneg, delta=delta)
-        ost, orel = OP.pdhg(A, At, data, g.n, alpha, s, s, 1, nonneg=nonneg, state=ost)
+        plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, s, s, alpha, nonneg=nonneg, delta=delta,
+                       beta=beta, mean_target=0.2, fmean=fmean if beta > 0 else None)
+        ost, orel = OP.pdhg(A, At, data, g.n, alpha, s, s, 1, nonneg=nonneg, state=ost, mean_penalty=mp)
         torch.cuda.synchronize()
+        if beta > 0:
+            assert abs(float(fmean) - ost["f"].mean()) <= (k + 1) * OP_TOL * np.sqrt(np.mean(ost["f"] ** 2))
         tol = (k + 1) * OP_TOL
         for name in ("f", "fbar", "y"):
             assert rel(st[name].double().cpu().numpy(), ost[name]) <= tol, (k, name)
@@ -136,6 +143,26 @@ def test_pdhg_stop_rule_matches_oracle(cuda_dev):
     assert rel(f.double().cpu().numpy(), st["f"]) <= 1e-3
 
 
+def test_pdhg_mouse_variant_reconstruct(cuda_dev):
+    """pdhg_reconstruct with nonneg=False and the mean penalty: the mean it
+    keeps on the device is the image's mean, the penalty pulls the mean towards
+    its target, and the iterates follow the oracle."""
+    g = Geometry(64, 48, 0.3, 1.5 * math.pi, 96, 2.0, 128)
+    data = _data(g, seed=5)
+    plan = PatPlan(g, device=cuda_dev)
+    gd = torch.tensor(data, dtype=torch.float32, device=cuda_dev)
+    s = 0.99 / math.sqrt(_oracle_norm_sq(g) + 8.0)
+    iters = 30
+    f0, _, _ = pdhg_reconstruct(plan, gd, 1e-3, iters=iters, sigma=s, tau=s, nonneg=False, stop_tol=0.0)
+    f1, _, st = pdhg_reconstruct(plan, gd, 1e-3, iters=iters, sigma=s, tau=s, nonneg=False,
+                                 mean_penalty=(400.0, 0.5), stop_tol=0.0)
+    assert abs(float(st["fmean"]) - float(f1.mean())) <= 1e-6 * float(f1.abs().max())
+    assert abs(float(f1.mean()) - 0.5) < abs(float(f0.mean()) - 0.5)
+    ost, _ = OP.pdhg(lambda x: O.forward(og(g), x), lambda y: O.adjoint(og(g), y), data, g.n, 1e-3, s, s, iters,
+                     nonneg=False, mean_penalty=(400.0, 0.5))
+    assert rel(f1.double().cpu().numpy(), ost["f"]) <= iters * OP_TOL
+
+
 def test_pdhg_argument_checks(cuda_dev):
     from paper_2604_19176_gb300._lib import PatError
 
@@ -151,6 +178,11 @@ def test_pdhg_argument_checks(cuda_dev):
         plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.0, 0.1, 1e-3)
     with pytest.raises(PatError):   # negative weight
         plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, -1.0)
+    with pytest.raises(PatError):   # mean penalty without the mean buffer
+        plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, 1e-3, beta=1.0)
+    with pytest.raises(PatError):   # mean buffer inside f
+        plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, 1e-3, beta=1.0,
+                       fmean=st["f"].view(-1)[:1])
     bf = PatPlan(g, device=cuda_dev, image_dtype=torch.bfloat16)
     with pytest.raises(PatError):   # FP32 plans only
         bf.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, 1e-3)
