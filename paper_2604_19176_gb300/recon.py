@@ -18,6 +18,8 @@
 * :func:`pdhg_reconstruct` — Eq. (4) with the unsmoothed TV, solved by the
   primal-dual hybrid gradient method the paper uses (Sec. 2.1), one
   ``pat_pdhg_step`` per iteration, same stopping rule.
+* :func:`initial_reconstruction` — an approximate inverse (A^T, Landweber or
+  CGLS) as the DIP network input in place of random noise (Sec. 2.2).
 """
 from __future__ import annotations
 
@@ -32,7 +34,7 @@ import torch.nn.functional as F
 from .api import PatPlan
 
 __all__ = ["PatOperator", "TVFunction", "UNet", "operator_norm_sq", "dip_reconstruct", "tv_reconstruct", "pat_apply",
-           "tv_value", "pdhg_steps", "pdhg_reconstruct"]
+           "tv_value", "pdhg_steps", "pdhg_reconstruct", "initial_reconstruction"]
 
 
 class PatOperator(torch.autograd.Function):
@@ -224,6 +226,71 @@ def pdhg_reconstruct(plan: PatPlan, g: torch.Tensor, alpha: float, iters: int = 
             if k > 0 and r <= stop_tol:
                 break
     return state["f"], hist, state
+
+
+class _Segments:
+    """Per-instance reductions and broadcasts over a plan's packed images / data."""
+
+    def __init__(self, plan: PatPlan):
+        dev = plan.device
+        fo, go = plan.layout()
+        n = len(plan.geoms)
+        self.n = n
+        self.f_idx = torch.repeat_interleave(torch.arange(n, device=dev),
+                                             torch.tensor([fo[i + 1] - fo[i] for i in range(n)], device=dev))
+        self.g_idx = torch.repeat_interleave(torch.arange(n, device=dev),
+                                             torch.tensor([go[i + 1] - go[i] for i in range(n)], device=dev))
+
+    def dot(self, a: torch.Tensor, b: torch.Tensor, image: bool) -> torch.Tensor:
+        idx = self.f_idx if image else self.g_idx
+        out = torch.zeros(self.n, dtype=torch.float64, device=a.device)
+        return out.index_add_(0, idx, (a.reshape(-1).double() * b.reshape(-1).double()))
+
+    def expand(self, v: torch.Tensor, image: bool, like: torch.Tensor) -> torch.Tensor:
+        idx = self.f_idx if image else self.g_idx
+        return v.float()[idx].reshape(like.shape)
+
+
+@torch.no_grad()
+def initial_reconstruction(plan: PatPlan, g: torch.Tensor, method: str = "cgls", iters: int = 10,
+                           omega: Optional[float] = None) -> torch.Tensor:
+    """Approximate inverse z ~ A^{-1} g for the DIP input (Sec. 2.2), standing in
+    for the paper's fast FFT-based inverse, which is not described there.
+
+    ``adjoint``: z = A^T g / ||A||^2.  ``landweber``: ``iters`` steps
+    f <- f + omega A^T (g - A f) from 0 (omega = 1 / ||A||^2 by default).
+    ``cgls``: ``iters`` conjugate-gradient steps on the normal equations from
+    0, with step lengths per instance.  A and A^T are the library's kernels;
+    the vector updates are plain tensor arithmetic, with FP64 inner products.
+    """
+    if method == "adjoint":
+        return plan.adjoint(g) / operator_norm_sq(plan)
+    if method == "landweber":
+        w = 1.0 / operator_norm_sq(plan) if omega is None else omega
+        f = torch.zeros(plan.image_shape(), dtype=torch.float32, device=plan.device)
+        for _ in range(iters):
+            f += w * plan.adjoint(g - plan.forward(f))
+        return f
+    if method != "cgls":
+        raise ValueError(f"unknown method {method!r}")
+    seg = _Segments(plan)
+    f = torch.zeros(plan.image_shape(), dtype=torch.float32, device=plan.device)
+    r = g.clone()
+    s = plan.adjoint(r)
+    p = s.clone()
+    gamma = seg.dot(s, s, True)
+    for _ in range(iters):
+        q = plan.forward(p)
+        qq = seg.dot(q, q, False)
+        a = torch.where(qq > 0, gamma / torch.where(qq > 0, qq, 1.0), 0.0)
+        f += seg.expand(a, True, f) * p
+        r -= seg.expand(a, False, r) * q
+        s = plan.adjoint(r)
+        gamma_new = seg.dot(s, s, True)
+        b = torch.where(gamma > 0, gamma_new / torch.where(gamma > 0, gamma, 1.0), 0.0)
+        p = s + seg.expand(b, True, p) * p
+        gamma = gamma_new
+    return f
 
 
 def dip_reconstruct(plan: PatPlan, g: torch.Tensor, z: torch.Tensor, lam: float = 1e-4, eps: float = 1e-3,
