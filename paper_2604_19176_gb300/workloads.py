@@ -102,5 +102,43 @@ def exp760_270() -> Workload:
                     {"phantom": "mixed", "tubes": 12, "gaussians": 5, "seeds": [9]})
 
 
+def fine_phantoms(wl: Workload, factor: int = 2) -> list[np.ndarray]:
+    """The workload's phantoms rendered on a ``factor`` times finer grid: the
+    same analytic objects (tube widths scaled in pixels so that they keep their
+    physical width)."""
+    params = dict(wl.params)
+    if "width_px" in params or params.get("phantom", "vessel") in ("vessel", "mixed"):
+        lo, hi = params.get("width_px", (2.0, 4.0))
+        params["width_px"] = (lo * factor, hi * factor)
+    return [make_phantom(g.n * factor, params.get("phantom", "vessel"), seed, params)
+            for g, seed in zip(wl.geometries, params.get("seeds", range(len(wl.geometries))))]
+
+
+def fine_geometries(wl: Workload, factor: int = 2) -> list[Geometry]:
+    """Each geometry on a ``factor`` times finer image grid, with the same
+    detectors and time grid (so the same data shape) and factor x K angles."""
+    return [Geometry(g.n * factor, g.n_det, g.arc_start, g.arc_span, g.n_t, g.t_max, g.n_angles * factor)
+            for g in wl.geometries]
+
+
+def simulate_fine_data(wl: Workload, factor: int = 2, device=None):
+    """Data for the workload's geometries simulated without the inverse crime:
+    A applied on a ``factor`` times finer grid to the finely rendered phantoms
+    (the paper simulated at 512^2 with a wave solver and reconstructed at 256^2,
+    Sec. 2.4.1; here the fine-grid A stands in for the wave solver).  Returns
+    the packed FP32 data on ``device``, shaped like a plan of ``wl``'s data."""
+    import torch
+
+    from .api import PatPlan
+
+    geoms = fine_geometries(wl, factor)
+    plan = PatPlan(geoms, device=device)
+    f = torch.tensor(np.concatenate([p.ravel() for p in fine_phantoms(wl, factor)]), dtype=torch.float32,
+                     device=plan.device).reshape(plan.image_shape())
+    out = plan.forward(f)
+    plan.close()
+    return out
+
+
 ALL = {w.__name__: w for w in (gauss64_full, vessel256_half, vessel512_half, batch64_uneven, vessel1024_b8,
                                exp760_270)}

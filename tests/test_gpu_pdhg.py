@@ -186,3 +186,22 @@ def test_pdhg_argument_checks(cuda_dev):
     bf = PatPlan(g, device=cuda_dev, image_dtype=torch.bfloat16)
     with pytest.raises(PatError):   # FP32 plans only
         bf.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, 1e-3)
+
+
+def test_fine_grid_data_no_inverse_crime(cuda_dev):
+    """Data simulated on a 2x finer grid (Sec. 2.4.1): the GPU's fine-grid data
+    match the oracle's A on the fine grid and the finely rendered phantom, and
+    differ from the coarse-grid data by a small but nonzero discretisation gap."""
+    from paper_2604_19176_gb300 import workloads
+    from paper_2604_19176_gb300.api import Geometry as G
+
+    wl = workloads.Workload("vessel64_half", (G(64, 48, 0.0, math.pi, 128, 2.0, 128),), "test",
+                            {"phantom": "vessel", "tubes": 6, "seeds": [3]})
+    fine = workloads.simulate_fine_data(wl, 2, device=cuda_dev).double().cpu().numpy()
+    fg = workloads.fine_geometries(wl, 2)[0]
+    fp = workloads.fine_phantoms(wl, 2)[0]
+    ref = O.forward(og(fg), fp.astype(np.float32).astype(np.float64))
+    assert rel(fine, ref) <= 1e-5
+    coarse = O.forward(og(wl.geometries[0]), wl.phantoms()[0])
+    gap = rel(coarse, ref)
+    assert 1e-4 < gap < 0.3
