@@ -205,3 +205,31 @@ def test_fine_grid_data_no_inverse_crime(cuda_dev):
     coarse = O.forward(og(wl.geometries[0]), wl.phantoms()[0])
     gap = rel(coarse, ref)
     assert 1e-4 < gap < 0.3
+
+
+def test_pdhg_full_size_vessel256(cuda_dev):
+    """The 256^2 limited-view workload (128 detectors on 180 degrees, 512 times,
+    K 512) at full size, in the launch configuration the benchmark uses: three
+    primal-dual iterations against the oracle's."""
+    from paper_2604_19176_gb300.workloads import vessel256_half
+
+    wl = vessel256_half()
+    g = wl.geometries[0]
+    plan = PatPlan(g, device=cuda_dev, tune=1)
+    O.set_threads(16)
+    try:
+        f = wl.phantoms()[0]
+        data = inputs.add_noise(O.forward(og(g), f), 0.05, seed=78).astype(np.float32).astype(np.float64)
+        s, alpha, iters = 0.3, 1e-3, 3
+        st = _gpu_state(plan, cuda_dev)
+        gd = torch.tensor(data, dtype=torch.float32, device=cuda_dev)
+        for _ in range(iters):
+            plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, s, s, alpha)
+        torch.cuda.synchronize()
+        ost, _ = OP.pdhg(lambda x: O.forward(og(g), x), lambda y: O.adjoint(og(g), y), data, g.n, alpha, s, s, iters)
+    finally:
+        O.set_threads(1)
+    for name in ("f", "y"):
+        assert rel(st[name].double().cpu().numpy(), ost[name]) <= iters * OP_TOL, name
+    p_gpu = np.stack([st["px"].double().cpu().numpy(), st["py"].double().cpu().numpy()])
+    assert rel(p_gpu, np.stack([ost["px"], ost["py"]])) <= iters * OP_TOL
