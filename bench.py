@@ -430,7 +430,7 @@ def precision_study(dev, stream, flush, with_oracle: bool) -> dict:
     phs = np.stack(wl.phantoms())
     res = {}
     for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
-        pp = PatPlan(geoms, device=dev, image_dtype=dt)
+        pp = PatPlan(geoms, device=dev, image_dtype=dt, tune=1)
         ft = torch.tensor(phs, dtype=dt, device=dev)
         go = torch.empty(pp.data_shape(), device=dev)
         fo = torch.empty(pp.image_shape(), dtype=dt, device=dev)
@@ -440,8 +440,10 @@ def precision_study(dev, stream, flush, with_oracle: bool) -> dict:
             pp.adjoint(go, out=fo)
 
         ms = _time_steps(fa, stream, flush, 5, warmup=2)
+        inf = pp.info()
         res[name] = {"instance_apps_per_s": len(geoms) * 1000.0 / ms, "ms_per_batch": ms,
-                     "samples_per_instance": pp.info()["samples"] // len(geoms)}
+                     "samples_per_instance": inf["samples"] // len(geoms),
+                     "tile": {k: inf[k] for k in ("m_lanes", "q_piece", "band_rows", "adj_mode", "adj_groups")}}
         del pp, ft, go, fo
         torch.cuda.empty_cache()
     g = geoms[0]

@@ -506,9 +506,18 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     if (cbps < 1) return PAT_ERR_UNSUPPORTED;
     const int64_t resident_warps = (int64_t)cbps * P.num_sms * 8;
     // adjoint list mode is chosen here (the sample count used for the budget is
-    // the forward's evaluated-sample upper bound); its groups split each list
+    // the forward's evaluated-sample upper bound); its groups split each list.
+    // Instances with the same geometry share one template's lists, so each
+    // template counts once.
     int64_t slot_samples_all = 0;
-    for (int i = 0; i < n_inst; ++i) slot_samples_all += tmpls[inst_tmpl[i]].slot_samples;
+    {
+        std::vector<char> seen(tmpls.size(), 0);
+        for (int i = 0; i < n_inst; ++i)
+            if (!seen[inst_tmpl[i]]) {
+                seen[inst_tmpl[i]] = 1;
+                slot_samples_all += tmpls[inst_tmpl[i]].slot_samples;
+            }
+    }
     // packed code lists (4 B per sample) when the code bits and the budget
     // allow (the fastest form measured), else fraction lists (12 B per
     // sample), else enumeration on every call

@@ -137,6 +137,10 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
         const int rows = (n_max + 1 + nb - 1) / nb + 1;
         if (rows <= max_rows && rows >= 3) rows_cands.push_back(rows);
     }
+    // large images: a few fixed band heights (the default budget gives short
+    // bands there, and units then cross many band edges)
+    for (int rows : {32, 48})
+        if (rows <= max_rows && 6 * (rows - 1) < n_max + 1) rows_cands.push_back(rows);
     Plan* best = nullptr;
     float best_ms = 1e30f;
     pat_options_t best_opt = opt;
