@@ -15,13 +15,14 @@
 // the forward's split-form expression.  Hits come out in the order (j, q, m).
 //
 // Three ways to run this:
-//   fraction lists (default when 12 B per sample fits the list budget): at
-//     plan creation the enumeration runs twice (count, then fill) to store
-//     every cell's hits as (Mbar index, a, b), a and b the exact FP32 values
-//     the forward computes; each call then streams the lists and gathers
-//     Mbar (one table load per sample, no coordinate arithmetic).
-//   code lists (4 B per sample): the hits as packed (j, m, q) codes; each
-//     call recomputes a and b from the codes with the forward's expressions.
+//   code lists (the default when 4 B per sample fits the list budget and a
+//     (j, m, q) code fits 32 bits): at plan creation the enumeration runs
+//     twice (count, then fill) to store every cell's hits as packed codes;
+//     each call streams the lists and recomputes a and b from the codes with
+//     the forward's expressions.
+//   fraction lists (12 B per sample): the hits as (Mbar index, a, b), a and b
+//     the exact FP32 values the forward computes (one table load per sample,
+//     no coordinate arithmetic, but a 3x larger stream).
 //   compute mode: the enumeration runs on every call (k_adj_cells), one warp
 //     per 8 x 4 patch of cells and detector group, partial Z per group.
 #include "device_common.cuh"
