@@ -333,6 +333,13 @@ pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, 
         !std::isfinite(alpha) || !(beta >= 0.f) || !std::isfinite(beta) || !std::isfinite(mean_target))
         return PAT_ERR_INVALID_ARG;
     if (beta > 0.f && !d_fmean) return PAT_ERR_INVALID_ARG;
+    if (d_delta) {
+        const size_t db = 2 * sizeof(float) * (size_t)p->n_inst;
+        if (reinterpret_cast<uintptr_t>(d_delta) & 3u) return PAT_ERR_INVALID_ARG;
+        for (float* q : img)
+            if (overlap(q, fb, d_delta, db)) return PAT_ERR_INVALID_ARG;
+        if (overlap(d_y, gb, d_delta, db) || overlap(d_g, gb, d_delta, db)) return PAT_ERR_INVALID_ARG;
+    }
     if (d_fmean) {
         const size_t mb = sizeof(float) * (size_t)p->n_inst;
         if (reinterpret_cast<uintptr_t>(d_fmean) & 3u) return PAT_ERR_INVALID_ARG;
