@@ -180,6 +180,9 @@ def test_pdhg_argument_checks(cuda_dev):
         plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, -1.0)
     with pytest.raises(PatError):   # mean penalty without the mean buffer
         plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, 1e-3, beta=1.0)
+    with pytest.raises(PatError):   # delta inside f
+        plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, 1e-3,
+                       delta=st["f"].view(-1)[:2])
     with pytest.raises(PatError):   # mean buffer inside f
         plan.pdhg_step(st["f"], st["fbar"], st["y"], st["px"], st["py"], gd, 0.1, 0.1, 1e-3, beta=1.0,
                        fmean=st["f"].view(-1)[:1])
