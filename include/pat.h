@@ -64,7 +64,7 @@ typedef enum {
     PAT_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or geometry        */
     PAT_ERR_CUDA = 2,        /* CUDA runtime error while enqueueing / creating  */
     PAT_ERR_OOM = 3,         /* device or host allocation failed                */
-    PAT_ERR_UNSUPPORTED = 4, /* valid request this build does not implement     */
+    PAT_ERR_UNSUPPORTED = 4, /* valid request the library does not implement    */
     PAT_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
     PAT_ERR_BAD_PLAN = 6     /* NULL, destroyed or foreign plan handle          */
 } pat_status_t;
