@@ -22,7 +22,7 @@
 // 16-byte load), kStages - 1 chunks ahead of the FMAs: a CTA's loads are all
 // in flight at once for short contractions.
 //
-// When a plan has fewer tiles than SMs, a thread-block cluster of 2 or 4 CTAs
+// When a plan has fewer tiles than SMs, a thread-block cluster of 2, 4 or 8 CTAs
 // shares each tile: rank r takes the r-th share of the chunks, and rank 0
 // adds the partial tiles in rank order through distributed shared memory
 // (deterministic; no global atomics).
