@@ -182,11 +182,12 @@ def make_inputs(seed_offset: int = 0):
     return wl, g, f_true
 
 
-def cpu_oracle_timing(g, f_true, budget_s: float = 12.0):
-    """FP64 oracle A + A^T on the host cores, bounded sample of detectors."""
+def cpu_oracle_timing(g, f_true, budget_s: float = 12.0, threads: int = 0):
+    """FP64 oracle A + A^T on the host cores (all of them, or ``threads``),
+    bounded sample of detectors."""
     import oracle as O
 
-    cores = os.cpu_count() or 1
+    cores = threads if threads > 0 else (os.cpu_count() or 1)
     O.set_threads(cores)
     og = O.Geometry(g.n, g.n_det, g.arc_start, g.arc_span, g.n_t, g.t_max, g.n_angles)
     # calibrate on a detector subset, then scale to the full detector count
@@ -413,7 +414,29 @@ def run_extras(dev, flush, with_oracle: bool = True) -> dict:
     del op, pb
     torch.cuda.empty_cache()
     out["precision_1024_b8"] = precision_study(dev, stream, flush, with_oracle)
+    if with_oracle:
+        out["oracle_cpu"] = oracle_cpu_table()
     return out
+
+
+def oracle_cpu_table() -> dict:
+    """The FP64 oracle's A + A^T applications/s on the host, single-threaded and
+    on all cores, for the 64^2 full-circle and the 256^2 limited-view workloads
+    (bounded samples of a few seconds each; context, not a target)."""
+    from paper_2604_19176_gb300 import workloads
+
+    res = {}
+    for wl in (workloads.gauss64_full(), workloads.vessel256_half()):
+        g = wl.geometries[0]
+        f = wl.phantoms()[0]
+        one = cpu_oracle_timing(g, f, budget_s=3.0, threads=1)
+        res[wl.name] = {"single_thread": one["value"], "sample_single": one["sample"]}
+        if wl.name == "gauss64_full":
+            allc = cpu_oracle_timing(g, f, budget_s=3.0)
+            res[wl.name].update({"all_cores": allc["value"], "cores": allc["cores"]})
+    res["unit"] = UNIT
+    res["note"] = "vessel256_half on all cores is the cpu_baseline of this line"
+    return res
 
 
 def precision_study(dev, stream, flush, with_oracle: bool) -> dict:
