@@ -42,20 +42,22 @@ UNIT = "applications/s"
 LAM, EPS, NOISE = 1e-3, 1e-3, 0.01
 SMEM_BYTES_PER_CLK_SM = 128        # shared-memory load bandwidth per SM per clock (32 banks x 4 B)
 BYTES_PER_SAMPLE = 16              # 4 FP32 texels per bilinear sample
+CLOCK_WINDOW_S = 0.5               # load before and after the timed steps while clocks are sampled
 
 
 def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--profile", action="store_true", help="short run for ncu captures (no flush, no extras)")
     p.add_argument("--tile", default="",
-                   help="fixed tile shape m_lanes,q_piece,band_rows,adj_groups,adj_mode,abel_split instead of "
-                        "the autotuner (e.g. the tile_shape a previous run reported), for reproducible profiles")
+                   help="fixed tile shape m_lanes,q_piece,band_rows,adj_groups,adj_mode,abel_split[,tile_cols] "
+                        "instead of the autotuner (e.g. the tile_shape a previous run reported), for reproducible "
+                        "profiles")
     return p.parse_args(argv)
 
 
@@ -147,11 +149,12 @@ def load_peaks():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources, to invalidate stored ncu traffic after a change."""
+    """Hash of the library sources (kernels and the host code that lays out
+    their tables), to invalidate stored ncu traffic after a change."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2604_19176_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -182,58 +185,75 @@ def make_inputs(seed_offset: int = 0):
     return wl, g, f_true
 
 
-def cpu_oracle_timing(g, f_true, budget_s: float = 12.0, threads: int = 0):
-    """FP64 oracle A + A^T on the host cores (all of them, or ``threads``),
-    bounded sample of detectors."""
+def cpu_oracle_timing(g, f_true, budget_s: float = 12.0, threads: int = 0, max_reps: int = 50):
+    """FP64 oracle A + A^T of the whole workload (every detector, no scaling)
+    on the host cores (all of them, or ``threads``): as many applications as
+    fit in about ``budget_s`` seconds (at least one)."""
     import oracle as O
 
     cores = threads if threads > 0 else (os.cpu_count() or 1)
     O.set_threads(cores)
     og = O.Geometry(g.n, g.n_det, g.arc_start, g.arc_span, g.n_t, g.t_max, g.n_angles)
-    # calibrate on a detector subset, then scale to the full detector count
-    sub = max(8, min(g.n_det, 32))
-    gs = O.Geometry(g.n, sub, g.arc_start, g.arc_span * sub / g.n_det, g.n_t, g.t_max, g.n_angles)
-    d = np.random.default_rng(0).standard_normal((sub, g.n_t))
+    d = np.random.default_rng(0).standard_normal((g.n_det, g.n_t))
     t0 = time.perf_counter()
     reps = 0
     while True:
-        O.forward(gs, f_true)
-        O.adjoint(gs, d)
+        O.forward(og, f_true)
+        O.adjoint(og, d)
         reps += 1
-        if time.perf_counter() - t0 > budget_s or reps >= 50:
+        if time.perf_counter() - t0 > budget_s or reps >= max_reps:
             break
     dt = (time.perf_counter() - t0) / reps
-    per_app = dt * g.n_det / sub
     O.set_threads(1)
-    return {"value": 1.0 / per_app, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} x (A + A^T) on {sub} of {g.n_det} detectors (same N, n_t, K), "
-                      f"time scaled by {g.n_det}/{sub}; FP64, OpenMP over detectors"}
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} x (A + A^T) of the whole workload ({g.n_det} detectors, N={g.n}, n_t={g.n_t}, "
+                      f"K={g.n_angles}); FP64, OpenMP over detectors, {cores} threads"}
+
+
+def workload_config(g) -> dict:
+    """The `config` object both arms print."""
+    return {"workload": WORKLOAD, "N": g.n, "n_det": g.n_det, "arc_deg": 180, "n_t": g.n_t, "K": g.n_angles,
+            "lambda": LAM, "tv_eps": EPS, "noise": "1% of max|g|",
+            "l2": "flushed (256 MB write) before every timed step, outside the events",
+            "step": "one A + A^T application (GPU: pat_tv_step: A f, residual, A^T r, TV gradient, update)"}
 
 
 def reference_arm(args):
+    """The FP64 oracle, as it stands, on the host cores: K steps after W
+    warm-up steps, each step one whole A + A^T application of the workload
+    (every detector), so the line's steps, metric and config are the GPU arm's."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import oracle as O
+
     wl, g, f_true = make_inputs()
-    # each step: a bounded sample of A + A^T, scaled to one application
     cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    og = O.Geometry(g.n, g.n_det, g.arc_start, g.arc_span, g.n_t, g.t_max, g.n_angles)
+    d = np.random.default_rng(0).standard_normal((g.n_det, g.n_t))
+
+    def step():
+        O.forward(og, f_true)
+        O.adjoint(og, d)
+
+    for _ in range(args.warmup):
+        step()
     per = []
-    budget = max(2.0, min(20.0, 120.0 / max(1, args.steps)))
-    if args.warmup > 0:
-        cpu_oracle_timing(g, f_true, budget_s=0.5)   # one short untimed sample (builds and loads the oracle)
-    steps = min(args.steps, 10)
-    for _ in range(steps):
-        r = cpu_oracle_timing(g, f_true, budget_s=budget / 4)
-        per.append(1.0 / r["value"])
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        per.append(time.perf_counter() - t0)
+    O.set_threads(1)
     ms = 1000.0 * statistics.mean(per)
     val = 1000.0 / ms
+    sample = (f"{args.steps} timed steps after {args.warmup} warm-up steps, each one A + A^T of the whole workload "
+              f"({g.n_det} detectors); FP64, OpenMP over detectors, {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": g.n, "n_det": g.n_det, "arc_deg": 180, "n_t": g.n_t,
-                       "K": g.n_angles, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": r["sample"]},
+            "config": workload_config(g),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -414,8 +434,86 @@ def run_extras(dev, flush, with_oracle: bool = True) -> dict:
     del op, pb
     torch.cuda.empty_cache()
     out["precision_1024_b8"] = precision_study(dev, stream, flush, with_oracle)
+    out["config_runs_256"] = config_runs(dev, stream)
     if with_oracle:
         out["oracle_cpu"] = oracle_cpu_table()
+    return out
+
+
+def config_runs(dev, stream) -> dict:
+    """The reconstruction runs the 256^2 limited-view configurations name:
+    500 fused projected-gradient TV iterations of Eq. (4) (lambda 1e-3,
+    eps 1e-3, f >= 0) at 1 % and 5 % noise, and 2000 Adam steps (lr 1e-4)
+    of the DIP loss of Eq. (5) (||A f - g||^2 + 1e-4 TV, 5 % noise, U-Net 4
+    levels / 32 channels, z ~ N(0, 0.1^2)).  Reported: the final objective,
+    the relative L2 error against the phantom, and the wall time."""
+    import torch
+
+    from paper_2604_19176_gb300 import PatPlan, inputs, workloads
+    from paper_2604_19176_gb300.recon import UNet, operator_norm_sq, pat_apply, tv_value
+
+    wl = workloads.vessel256_half()
+    g = wl.geometries[0]
+    f_np = wl.phantoms()[0]
+    plan = PatPlan(g, device=dev, tune=1)
+    f_true = torch.tensor(f_np, dtype=torch.float32, device=dev)
+    clean = plan.forward(f_true).double().cpu().numpy()
+    a2 = operator_norm_sq(plan)
+    out = {}
+
+    def objective(f, data, lam, eps, halve):
+        r = plan.forward(f).double() - data.double()
+        tv = float(plan.tv_value(f, eps)[0])
+        return (0.5 if halve else 1.0) * float((r * r).sum()) + lam * tv
+
+    for lvl, seed in ((0.01, 81), (0.05, 82)):
+        data = torch.tensor(inputs.add_noise(clean, lvl, seed=seed), dtype=torch.float32, device=dev)
+        tau = 1.0 / (a2 + 8.0 * LAM / EPS)
+        fa, fb = torch.zeros_like(f_true), torch.zeros_like(f_true)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(250):
+            plan.tv_step(fa, fb, data, tau, LAM, EPS, nonneg=True)
+            plan.tv_step(fb, fa, data, tau, LAM, EPS, nonneg=True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[f"tv500_noise{int(lvl * 100)}pct"] = {
+            "iterations": 500, "wall_s": wall, "objective_final": objective(fa, data, LAM, EPS, True),
+            "objective_initial": objective(torch.zeros_like(f_true), data, LAM, EPS, True),
+            "rel_l2_error_vs_phantom": float((fa - f_true).norm() / f_true.norm()),
+            "config": "Eq. (4): 1/2 ||A f - g||^2 + 1e-3 TV_eps (eps 1e-3), f >= 0, tau = 1/(||A||^2 + 8 lam/eps), "
+                      "pat_tv_step from zero, data A f_true + noise at the stated fraction of max|g|"}
+
+    data = torch.tensor(inputs.add_noise(clean, 0.05, seed=83), dtype=torch.float32, device=dev)
+    z = torch.tensor(inputs.dip_input(32, g.n, seed=3), dtype=torch.float32, device=dev)
+    torch.manual_seed(0)
+    net = UNet(in_ch=32, base=32).to(dev)
+    opt = torch.optim.Adam(net.parameters(), lr=1e-4)
+    losses = torch.zeros(2000, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(2000):
+        opt.zero_grad(set_to_none=True)
+        f = net(z).reshape(g.n, g.n)
+        r = pat_apply(f, plan) - data
+        loss = (r * r).sum() + 1e-4 * tv_value(f, plan, 1e-3).sum()
+        loss.backward()
+        opt.step()
+        losses[k] = loss.detach()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    with torch.no_grad():
+        f = net(z).reshape(g.n, g.n)
+    lc = losses.cpu().numpy()
+    out["dip2000_noise5pct"] = {
+        "steps": 2000, "wall_s": wall, "iters_per_s": 2000 / wall,
+        "loss_first": float(lc[0]), "loss_min": float(lc.min()), "loss_last": float(lc[-1]),
+        "loss_at": {str(k): float(lc[k]) for k in (0, 99, 499, 999, 1499, 1999)},
+        "rel_l2_error_vs_phantom": float((f - f_true).norm() / f_true.norm()),
+        "config": "Eq. (5): ||A f_theta - g||^2 + 1e-4 TV_eps (eps 1e-3), U-Net 4 levels / 32 base channels FP32 "
+                  "(TF32 off), z ~ N(0, 0.1^2) 1x32x256x256, Adam lr 1e-4, 5 % noise"}
+    del net, opt, plan
+    torch.cuda.empty_cache()
     return out
 
 
@@ -522,9 +620,11 @@ def main():
 
     wl, g, f_true = make_inputs(seed_offset=rank)
     if args.tile:
-        ml, qp, br, ag, am, sp = (int(x) for x in args.tile.split(","))
+        vals = [int(x) for x in args.tile.split(",")]
+        ml, qp, br, ag, am, sp = vals[:6]
+        tc = vals[6] if len(vals) > 6 else 0
         plan = PatPlan(g, device=dev, m_lanes=ml, q_piece=qp, band_rows=br, adj_groups=ag, adj_mode=am,
-                       abel_split=sp)
+                       abel_split=sp, tile_cols=tc)
     else:
         plan = PatPlan(g, device=dev, tune=1)  # autotuned tile shapes (timed at plan creation)
     info = plan.info()
@@ -565,10 +665,28 @@ def main():
     clocks = ClockSampler(dev.index)
     n_steps = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+
+    def load_for(seconds: float):
+        # the same flushed steps, untimed, back to back for `seconds` (wall)
+        t_end = time.perf_counter() + seconds
+        i = 0
+        while time.perf_counter() < t_end:
+            for _ in range(50):
+                flush.fill_(float(i))
+                step()
+                i += 1
+            torch.cuda.synchronize()
+
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    # The timed region lasts a few ms, shorter than the sampling period of
+    # nvidia-smi: the clocks are sampled over a window of identical load steps
+    # that contains it (CLOCK_WINDOW_S of them before and after).
+    if not args.profile:
+        clocks.start()
+        load_for(CLOCK_WINDOW_S)
+    torch.cuda.synchronize()
     if args.profile:
         torch.cuda.profiler.start()   # ncu --profile-from-start off: capture the timed steps only
     for i in range(n_steps):
@@ -582,7 +700,11 @@ def main():
         torch.cuda.profiler.stop()
     if world > 1:
         torch.distributed.barrier()
+    if not args.profile:
+        load_for(CLOCK_WINDOW_S)
     clk = clocks.stop()
+    clk["window"] = (f"nvidia-smi every 20 ms over {CLOCK_WINDOW_S:.1f} s of identical steps, the timed "
+                     f"steps, and {CLOCK_WINDOW_S:.1f} s more")
     step_ms = [a.elapsed_time(b) for a, b in ev]
     # Per-kernel durations for the roofline: a second pass of the same steps
     # with an event pair around every kernel (the events themselves cost a few
@@ -670,14 +792,11 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": g.n, "n_det": g.n_det, "arc_deg": 180, "n_t": g.n_t,
-                           "K": g.n_angles, "lambda": LAM, "tv_eps": EPS, "noise": "1% of max|g|",
-                           "l2": "flushed (256 MB write) before every timed step, outside the events",
-                           "step": "pat_tv_step: A f, residual, A^T r, TV gradient, projected update"},
+                "config": workload_config(g),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * n_steps,
-                "tile_shape": {k: info[k] for k in ("m_lanes", "q_piece", "band_rows", "bands_max", "adj_groups",
-                                                    "adj_mode", "abel_split_fwd", "abel_split_adj")},
+                "tile_shape": {k: info[k] for k in ("m_lanes", "q_piece", "band_rows", "tile_cols", "bands_max",
+                                                    "adj_groups", "adj_mode", "abel_split_fwd", "abel_split_adj")},
                 "samples_per_application": samples, "sample_slots": info["sample_slots"],
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
                 "extras": extras}

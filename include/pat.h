@@ -101,7 +101,7 @@ typedef struct {
                          /*     buffers, synchronises the stream; cached per process), 2 = 0  */
     int32_t m_lanes;     /* radii per warp in the circular-mean kernel (32, 16 or 8); 0=auto */
     int32_t q_piece;     /* max angular nodes per work unit (multiple of 4); 0 = auto        */
-    int32_t band_rows;   /* max image rows per shared-memory band; 0 = auto                  */
+    int32_t band_rows;   /* max pixel rows of a circular-mean tile; 0 = auto                 */
     int32_t adj_groups;  /* detector groups of the adjoint gather, 1..16; 0 = auto           */
     int32_t adj_mode;    /* adjoint gather: 0 = auto (1 if it fits the list budget, else 3,   */
                          /*   else 2), 1 = per-cell sample code lists built at creation       */
@@ -110,7 +110,8 @@ typedef struct {
                          /*   (~12 B per sample: Mbar index and the FP32 bilinear fractions)  */
     int32_t abel_split;  /* CTAs (a thread-block cluster) sharing each time-stage tile: 1, 2, */
                          /*   4 or 8; 0 = auto (more when there are fewer tiles than SMs)     */
-    int32_t reserved[7];
+    int32_t tile_cols;   /* max pixel columns of a circular-mean tile; 0 = auto               */
+    int32_t reserved[6];
 } pat_options_t;
 
 /* Plan statistics (pat_plan_info). */
@@ -125,13 +126,14 @@ typedef struct {
     int64_t work_units;      /* circular-mean work units                                  */
     int64_t device_bytes;    /* device memory held by the plan                            */
     int32_t m_lanes, q_piece, band_rows, adj_groups; /* tile shape in use              */
-    int32_t bands_max;       /* largest number of bands of any instance                   */
+    int32_t bands_max;       /* largest number of circular-mean tiles of any instance     */
     int32_t adj_mode;        /* adjoint gather in use: 1 = code lists, 2 = enumeration,   */
                              /*   3 = fraction lists                                      */
     int64_t list_bytes;      /* device memory of the adjoint sample lists                 */
     int32_t abel_split_fwd;  /* CTAs per forward / adjoint time-stage tile in use         */
     int32_t abel_split_adj;
-    int32_t reserved[2];
+    int32_t tile_cols;       /* widest circular-mean tile (pixels); band_rows the tallest */
+    int32_t reserved[1];
 } pat_plan_info_t;
 
 /*
@@ -189,8 +191,11 @@ pat_status_t pat_adjoint(pat_plan_t plan, const float* d_g, void* d_f, void* str
  *   column / row), the regulariser of Eq. (4) and Eq. (5).
  *   d_f:     device FP32 images (packed like pat_forward's input).
  *   eps:     smoothing, > 0.
- *   d_grad:  device FP32, overwritten with dTV/df (may be NULL).
- *   d_value: device FP32 array of n_instances values (may be NULL).
+ *   d_grad:  device FP32, overwritten with dTV/df (may be NULL); must not
+ *            overlap d_f (the stencil reads neighbours other threads may
+ *            already have written), else PAT_ERR_INVALID_ARG.
+ *   d_value: device FP32 array of n_instances values (may be NULL; not both
+ *            NULL); must not overlap d_f or d_grad.
  * FP32 plans only (PAT_ERR_UNSUPPORTED for BF16 plans).
  */
 pat_status_t pat_tv_grad(pat_plan_t plan, const float* d_f, float eps, float* d_grad,
@@ -276,8 +281,26 @@ pat_status_t pat_pdhg_step(pat_plan_t plan, float* d_f, float* d_fbar, float* d_
  * pat_plan_sync_status — synchronise the stream and report a device-side
  * error recorded by a bounded wait in a persistent launch (PAT_ERR_TIMEOUT),
  * clearing it.  Returns PAT_OK when none was recorded.
+ * A launch whose wait gave up returns early: the results of that call are
+ * undefined (some of its partial sums are missing), later calls are not
+ * affected (the circular-mean kernel keeps no state across calls; its work is
+ * scheduled statically).  The status word stays set until this call reports
+ * and clears it (it also re-arms the adjoint kernels' work queues, which no
+ * bounded wait can leave armed).
  */
 pat_status_t pat_plan_sync_status(pat_plan_t plan, void* stream);
+
+/*
+ * pat_plan_set_wait_probe — test hook for the failure path above.  With
+ * clocks > 0, the next circular-mean launch of this plan (pat_forward,
+ * pat_tv_step, pat_pdhg_step) has its first CTA wait, bounded by `clocks`
+ * SM clock cycles, on an mbarrier that nothing completes; the wait runs out,
+ * records PAT_ERR_TIMEOUT in the device status word and that CTA returns
+ * (no copy is in flight at that point, nothing faults).  The probe disarms
+ * itself after that one launch.  clocks = 0 disarms it; negative clocks
+ * return PAT_ERR_INVALID_ARG.  Synchronous with respect to the host only.
+ */
+pat_status_t pat_plan_set_wait_probe(pat_plan_t plan, int32_t clocks);
 
 /*
  * Per-kernel timing (tracing).  When enabled, every kernel the plan enqueues
@@ -308,16 +331,23 @@ pat_status_t pat_plan_kernel_times(pat_plan_t plan, double* total_ms, int64_t* l
  *   d_f:     device FP32, batch images of n x n, row-major, packed (read only).
  *   n:       image side, 1..16384.        batch: number of images, >= 1.
  *   eps:     smoothing, > 0.
- *   d_grad:  device FP32, same layout as d_f, overwritten with dTV/df (may be NULL).
- *   d_value: device FP32, batch values (may be NULL; not both NULL).
+ *   d_grad:  device FP32, same layout as d_f, overwritten with dTV/df (may be
+ *            NULL); must not overlap d_f (the stencil reads neighbours other
+ *            threads may already have written), else PAT_ERR_INVALID_ARG.
+ *   d_value: device FP32, batch values (may be NULL; not both NULL); must not
+ *            overlap d_f or d_grad.
  *   Pointers 4-byte aligned, owned by the caller.
- * Scratch: a fixed static device array of PAT_TV_NOALLOC_MAX_TILES floats
- * (256 KB), one per 32 x 8 tile: batch * ceil(n/32) * ceil(n/8) must not
+ * Scratch: the value (and only the value) needs one partial sum per 32 x 8
+ * tile, kept in a fixed static device array of PAT_TV_NOALLOC_MAX_TILES
+ * floats (256 KB).  With d_value set, batch * ceil(n/32) * ceil(n/8) must not
  * exceed PAT_TV_NOALLOC_MAX_TILES, else PAT_ERR_INVALID_ARG and nothing is
- * enqueued (e.g. n = 256 allows batch <= 256, n = 1024 allows batch <= 16).
- * The first call on a device looks up the array's device address (with that
- * device current); make it before any stream capture.  All calls share the
- * array, so calls that overlap on the GPU race; order them on one stream.
+ * enqueued: n = 256 allows batch <= 256, n = 1024 batch <= 16, n = 4096 batch 1,
+ * and no batch for n > 4096.  Gradient-only calls (d_value NULL) use no
+ * scratch and take every n and batch.
+ * The first call with d_value set on a device looks up the array's device
+ * address (with that device current); make it before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU race; order them
+ * on one stream.
  */
 #define PAT_TV_NOALLOC_MAX_TILES 65536
 pat_status_t pat_tv_grad_noalloc(const float* d_f, int32_t n, int32_t batch, float eps, float* d_grad,

@@ -23,7 +23,7 @@ EXPORTED = (
     "pat_plan_create", "pat_plan_destroy", "pat_plan_layout", "pat_plan_info", "pat_forward",
     "pat_adjoint", "pat_tv_grad", "pat_residual", "pat_descent_step", "pat_plan_sync_status",
     "pat_plan_set_timing", "pat_plan_kernel_times", "pat_tv_grad_noalloc", "pat_tv_step", "pat_pdhg_step",
-    "pat_status_string",
+    "pat_plan_set_wait_probe", "pat_status_string",
 )
 KERNEL_KINDS = ("circmean", "abel_fwd", "abel_adj", "adjoint_gather", "tv", "residual", "descent", "tv_update",
                 "pdhg_dual", "pdhg_primal")
@@ -42,7 +42,7 @@ class PatOptions(ctypes.Structure):
         ("image_dtype", ctypes.c_int32), ("schedule", ctypes.c_int32), ("tune", ctypes.c_int32),
         ("m_lanes", ctypes.c_int32), ("q_piece", ctypes.c_int32), ("band_rows", ctypes.c_int32),
         ("adj_groups", ctypes.c_int32), ("adj_mode", ctypes.c_int32), ("abel_split", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("tile_cols", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -54,7 +54,7 @@ class PatPlanInfo(ctypes.Structure):
         ("m_lanes", ctypes.c_int32), ("q_piece", ctypes.c_int32), ("band_rows", ctypes.c_int32),
         ("adj_groups", ctypes.c_int32), ("bands_max", ctypes.c_int32), ("adj_mode", ctypes.c_int32),
         ("list_bytes", ctypes.c_int64), ("abel_split_fwd", ctypes.c_int32), ("abel_split_adj", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("tile_cols", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pat_descent_step.argtypes = [vp, vp, vp, vp, f32, f32, i32, vp, vp]
     lib.pat_plan_sync_status.argtypes = [vp, vp]
     lib.pat_plan_set_timing.argtypes = [vp, i32]
+    lib.pat_plan_set_wait_probe.argtypes = [vp, i32]
     lib.pat_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i64p, i32]
     lib.pat_tv_grad_noalloc.argtypes = [vp, i32, i32, f32, vp, vp, vp]
     lib.pat_tv_step.argtypes = [vp, vp, vp, vp, f32, f32, f32, i32, vp, vp]

@@ -51,13 +51,14 @@ class PatPlan:
     """Owner of a ``pat_plan_t`` for a list of geometries on one CUDA device.
 
     image_dtype: torch.float32 or torch.bfloat16 (storage of f in forward/adjoint).
-    Tile options (m_lanes, q_piece, band_rows, adj_groups) map to
-    ``pat_options_t``; 0 selects the built-in choice.
+    Tile options (m_lanes, q_piece, band_rows, tile_cols, adj_groups, ...) map
+    to ``pat_options_t``; 0 selects the built-in choice.
     """
 
     def __init__(self, geoms: Geometry | Sequence[Geometry], *, image_dtype=torch.float32, device=None,
                  m_lanes: int = 0, q_piece: int = 0, band_rows: int = 0, adj_groups: int = 0,
-                 adj_mode: int = 0, abel_split: int = 0, schedule: int = 0, tune: int = 0, stream=None):
+                 adj_mode: int = 0, abel_split: int = 0, tile_cols: int = 0, schedule: int = 0, tune: int = 0,
+                 stream=None):
         self._lib = _lib.load()
         if isinstance(geoms, Geometry):
             geoms = [geoms]
@@ -76,6 +77,7 @@ class PatPlan:
         opt.m_lanes, opt.q_piece, opt.band_rows, opt.adj_groups = m_lanes, q_piece, band_rows, adj_groups
         opt.adj_mode = adj_mode
         opt.abel_split = abel_split
+        opt.tile_cols = tile_cols
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = _stream_ptr(stream, self.device)
@@ -272,6 +274,11 @@ class PatPlan:
 
     def sync_status(self, stream=None) -> int:
         return int(self._lib.pat_plan_sync_status(self._h, _stream_ptr(stream, self.device)))
+
+    def set_wait_probe(self, clocks: int) -> None:
+        """Test hook: the next circular-mean launch has one CTA wait on a barrier
+        nothing completes, bounded by ``clocks`` SM cycles (see pat_plan_set_wait_probe)."""
+        _lib.check("pat_plan_set_wait_probe", self._lib.pat_plan_set_wait_probe(self._h, int(clocks)))
 
 
 def geometry_from(obj) -> Geometry:

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel(DevPlan dp, const f
     int a_pitch, a_len, b_pitch, k_begin, k_end;
     if (FWD) {
         A = dp.msum + in.mbar_off;
-        a_pitch = in.n_rp;
+        a_pitch = in.m_pitch;
         a_len = in.n_r;
         B = dp.P + in.p_off + (size_t)in.n_tp * in.n_rp;
         b_pitch = in.n_tp;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kAbelWarps * kWarp) k_abel(DevPlan dp, const f
             for (int i = 0; i < 4; ++i) {
                 const int j = t.j0 + 4 * w + i;
                 if (j >= in.n_det) break;
-                dp.mbar[in.mbar_off + (size_t)j * in.n_rp + x] = r4[i];
+                dp.mbar[in.mbar_off + (size_t)j * in.m_pitch + x] = r4[i];
             }
         }
     }

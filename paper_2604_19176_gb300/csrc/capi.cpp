@@ -9,6 +9,7 @@
 #include <set>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "kernels.h"
 #include "pat.h"
@@ -31,6 +32,13 @@ Plan* lookup(pat_plan_t h)
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// true when the byte ranges [a, a + na) and [b, b + nb) overlap
+bool overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
 // Makes the plan's device current for the duration of a call.
 struct DeviceScope {
     int prev = -1;
@@ -52,6 +60,15 @@ struct DeviceScope {
 };
 
 pat_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? PAT_OK : PAT_ERR_CUDA; }
+
+// NVTX range named after the entry point, for the host-side timeline of a
+// profiler (header-only NVTX: a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 cudaEvent_t take_event(Plan& p)
 {
@@ -80,6 +97,15 @@ cudaError_t timed(Plan& p, int kind, cudaStream_t st, F&& fn)
         p.event_pool.push_back(a);
         p.event_pool.push_back(b);
     }
+    return e;
+}
+
+// The circular-mean launch; a wait probe armed by pat_plan_set_wait_probe
+// goes with this one launch only.
+cudaError_t circmean(Plan& p, const void* f, cudaStream_t st)
+{
+    const cudaError_t e = launch_circmean(p.dp, f, st);
+    p.dp.wait_probe = 0;
     return e;
 }
 
@@ -116,6 +142,7 @@ const char* pat_status_string(pat_status_t s)
 pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, const pat_options_t* opt_in,
                              void* stream, pat_plan_t* out)
 {
+    NvtxRange nvtx("pat_plan_create");
     if (!geoms || n_instances < 1 || n_instances > (1 << 20) || !out) return PAT_ERR_INVALID_ARG;
     pat_options_t opt;
     if (opt_in) opt = *opt_in;
@@ -128,7 +155,8 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
     if (opt.m_lanes != 32 && opt.m_lanes != 16 && opt.m_lanes != 8) return PAT_ERR_INVALID_ARG;
     if (opt.q_piece == 0) opt.q_piece = 128;
     if (opt.q_piece < 4 || opt.q_piece % 4 != 0) return PAT_ERR_INVALID_ARG;
-    if (opt.band_rows != 0 && (opt.band_rows < 3 || opt.band_rows > 8192)) return PAT_ERR_INVALID_ARG;
+    if (opt.band_rows != 0 && (opt.band_rows < 1 || opt.band_rows > 8192)) return PAT_ERR_INVALID_ARG;
+    if (opt.tile_cols != 0 && (opt.tile_cols < 1 || opt.tile_cols > 8192)) return PAT_ERR_INVALID_ARG;
     if (opt.adj_groups < 0 || opt.adj_groups > 16) return PAT_ERR_INVALID_ARG;
     if (opt.adj_mode < 0 || opt.adj_mode > 3) return PAT_ERR_INVALID_ARG;
     if (opt.abel_split != 0 && opt.abel_split != 1 && opt.abel_split != 2 && opt.abel_split != 4 &&
@@ -173,6 +201,7 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
 
 pat_status_t pat_plan_destroy(pat_plan_t h)
 {
+    NvtxRange nvtx("pat_plan_destroy");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     {
@@ -208,19 +237,21 @@ pat_status_t pat_plan_info(pat_plan_t h, pat_plan_info_t* info)
 
 pat_status_t pat_forward(pat_plan_t h, const void* d_f, float* d_g, void* stream)
 {
+    NvtxRange nvtx("pat_forward");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     if (!d_f || !d_g || !aligned16(d_f) || !aligned16(d_g)) return PAT_ERR_INVALID_ARG;
     DeviceScope ds(p->device);
     if (!ds.ok) return PAT_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return launch_circmean(p->dp, d_f, st); });
+    cudaError_t e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return circmean(*p, d_f, st); });
     if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_FWD, st, [&] { return launch_abel_fwd(p->dp, d_g, st); });
     return cuda_status(e);
 }
 
 pat_status_t pat_adjoint(pat_plan_t h, const float* d_g, void* d_f, void* stream)
 {
+    NvtxRange nvtx("pat_adjoint");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     if (!d_f || !d_g || !aligned16(d_f) || !aligned16(d_g)) return PAT_ERR_INVALID_ARG;
@@ -234,12 +265,18 @@ pat_status_t pat_adjoint(pat_plan_t h, const float* d_g, void* d_f, void* stream
 
 pat_status_t pat_tv_grad(pat_plan_t h, const float* d_f, float eps, float* d_grad, float* d_value, void* stream)
 {
+    NvtxRange nvtx("pat_tv_grad");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     if (p->dp.bf16) return PAT_ERR_UNSUPPORTED;
     if (!d_f || !aligned16(d_f) || !(eps > 0.f) || !std::isfinite(eps)) return PAT_ERR_INVALID_ARG;
     if (!d_grad && !d_value) return PAT_ERR_INVALID_ARG;
     if ((d_grad && !aligned16(d_grad)) || (d_value && (reinterpret_cast<uintptr_t>(d_value) & 3u)))
+        return PAT_ERR_INVALID_ARG;
+    // the stencil reads neighbours other threads may already have written
+    const size_t fb = sizeof(float) * (size_t)p->f_offsets.back(), vb = sizeof(float) * (size_t)p->n_inst;
+    if (d_grad && overlap(d_f, fb, d_grad, fb)) return PAT_ERR_INVALID_ARG;
+    if (d_value && (overlap(d_f, fb, d_value, vb) || (d_grad && overlap(d_grad, fb, d_value, vb))))
         return PAT_ERR_INVALID_ARG;
     DeviceScope ds(p->device);
     if (!ds.ok) return PAT_ERR_CUDA;
@@ -249,6 +286,7 @@ pat_status_t pat_tv_grad(pat_plan_t h, const float* d_f, float eps, float* d_gra
 
 pat_status_t pat_residual(pat_plan_t h, const float* d_Af, const float* d_g, float* d_r, float scale, void* stream)
 {
+    NvtxRange nvtx("pat_residual");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     if (!d_Af || !d_g || !d_r || !aligned16(d_Af) || !aligned16(d_g) || !aligned16(d_r) || !std::isfinite(scale))
@@ -263,6 +301,7 @@ pat_status_t pat_residual(pat_plan_t h, const float* d_Af, const float* d_g, flo
 pat_status_t pat_descent_step(pat_plan_t h, float* d_f, const float* d_adj, const float* d_tvgrad, float tau,
                               float lam, int32_t nonneg, float* d_delta, void* stream)
 {
+    NvtxRange nvtx("pat_descent_step");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     if (p->dp.bf16) return PAT_ERR_UNSUPPORTED;
@@ -280,6 +319,7 @@ pat_status_t pat_descent_step(pat_plan_t h, float* d_f, const float* d_adj, cons
 pat_status_t pat_tv_step(pat_plan_t h, const float* d_f_in, float* d_f_out, const float* d_g, float tau, float lam,
                          float eps, int32_t nonneg, float* d_delta, void* stream)
 {
+    NvtxRange nvtx("pat_tv_step");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     if (p->dp.bf16) return PAT_ERR_UNSUPPORTED;
@@ -291,7 +331,7 @@ pat_status_t pat_tv_step(pat_plan_t h, const float* d_f_in, float* d_f_out, cons
     if (!ds.ok) return PAT_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const DevPlan& dp = p->dp;
-    cudaError_t e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return launch_circmean(dp, d_f_in, st); });
+    cudaError_t e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return circmean(*p, d_f_in, st); });
     if (e == cudaSuccess)
         e = timed(*p, PAT_K_ABEL_FWD, st, [&] { return launch_abel_fwd(dp, p->d_resid, st, d_g); });
     if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, p->d_resid, st); });
@@ -302,19 +342,11 @@ pat_status_t pat_tv_step(pat_plan_t h, const float* d_f_in, float* d_f_out, cons
     return cuda_status(e);
 }
 
-namespace {
-// true when the byte ranges [a, a + na) and [b, b + nb) overlap
-bool overlap(const void* a, size_t na, const void* b, size_t nb)
-{
-    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
-    return x < y + nb && y < x + na;
-}
-} // namespace
-
 pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, float* d_px, float* d_py,
                            const float* d_g, float sigma, float tau, float alpha, int32_t nonneg, float beta,
                            float mean_target, float* d_fmean, float* d_delta, void* stream)
 {
+    NvtxRange nvtx("pat_pdhg_step");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     if (p->dp.bf16) return PAT_ERR_UNSUPPORTED;
@@ -355,7 +387,7 @@ pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, 
     const float inv1ps = 1.f / (1.f + sigma);
     cudaError_t e = timed(*p, PAT_K_PDHG_DUAL, st,
                           [&] { return launch_pdhg_dual_tv(dp, d_fbar, d_px, d_py, sigma, alpha, st); });
-    if (e == cudaSuccess) e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return launch_circmean(dp, d_fbar, st); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return circmean(*p, d_fbar, st); });
     if (e == cudaSuccess)
         e = timed(*p, PAT_K_ABEL_FWD, st, [&] { return launch_abel_fwd_dual(dp, d_y, d_g, sigma, inv1ps, st); });
     if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, d_y, st); });
@@ -371,6 +403,7 @@ pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, 
 
 pat_status_t pat_plan_sync_status(pat_plan_t h, void* stream)
 {
+    NvtxRange nvtx("pat_plan_sync_status");
     Plan* p = lookup(h);
     if (!p) return PAT_ERR_BAD_PLAN;
     DeviceScope ds(p->device);
@@ -386,6 +419,15 @@ pat_status_t pat_plan_sync_status(pat_plan_t h, void* stream)
     if (cudaMemsetAsync(p->d_counters, 0, p->counters_bytes, st) != cudaSuccess) return PAT_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
     return PAT_ERR_TIMEOUT;
+}
+
+pat_status_t pat_plan_set_wait_probe(pat_plan_t h, int32_t clocks)
+{
+    Plan* p = lookup(h);
+    if (!p) return PAT_ERR_BAD_PLAN;
+    if (clocks < 0) return PAT_ERR_INVALID_ARG;
+    p->dp.wait_probe = clocks;
+    return PAT_OK;
 }
 
 pat_status_t pat_plan_set_timing(pat_plan_t h, int32_t enable)

@@ -5,17 +5,38 @@
 // of f with zero outside the grid: the circular mean of the 2D Poisson
 // formula for the wave problem Eq. (1)-(2), discretised as in include/pat.h.
 //
-// Persistent CTAs.  The work is split into band tasks (an image band of one
-// instance and the units whose samples can fall in it).  CTA c works on band
-// tasks cta_seg[c] .. cta_seg[c+1]-1; for each it stages the band and the
-// instance's K ray directions in shared memory (TMA bulk copies, one per
-// image row and one for the rays, completing on an mbarrier) and
-// its warps take units, largest first, from the task's global queue, which
-// all CTAs assigned to the task share (the last one to finish re-arms it).
-// Lane l of a warp handles radius m0 + l % ML and angles
-// q0 + l / ML + i * (32 / ML); lanes walk along rays, so their 2 x 2 texel
-// reads are spatially coherent.  Each unit writes its own partial-sum slot,
-// so the result does not depend on scheduling.
+// Tiles.  Every image is partitioned into tiles of pixels.  A bilinear sample
+// is linear in the four pixels of its cell, so it is the sum over tiles of the
+// sample taken from a copy of the image in which only that tile's pixels are
+// kept (the rest zero).  A CTA working on a tile stages, for every cell
+// [c, c+1] x [r, r+1] that touches the tile, the coefficients of that partial
+// interpolant,
+//     f~(c + a, r + b) = c00 + a cx + b (cy + a cxy),
+//     c00 = f00, cx = f10 - f00, cy = f01 - f00, cxy = f11 - f10 - f01 + f00,
+// as one float4 (pixels outside the tile read as zero), so a sample costs one
+// 16-byte shared-memory load and three FMAs.  A sample's cell is clamped to
+// the staged block, whose outer ring of cells is all zero, so samples that
+// miss the tile add exactly zero and no per-sample test is needed.
+//
+// Work.  A unit is (detector j, ML consecutive radii, a range of angles) of
+// one tile; lane l handles radius m0 + l % ML and angles q0 + l / ML +
+// i * (32 / ML), walking along rays so that its cell reads are spatially
+// coherent.  CTA c works on tile tasks cta_seg[c] .. cta_seg[c+1]-1; for
+// each it stages the tile's cells (computed from f through L2) and the
+// instance's K ray directions (one TMA bulk copy on an mbarrier with a
+// bounded wait), and each of its warps processes the list of units the plan
+// assigned to it (balanced by their sample counts at plan time: a sample costs
+// the same everywhere, so no run-time queue is needed).  Each unit writes its
+// own partial-sum slot; k_msum then adds every (detector, radius block)'s
+// slots in slot order, so the result does not depend on scheduling and no
+// atomics or fences are needed.
+//
+// Sample position.  Split form (pat_internal.h): the cell index along u is
+// floor(fma(m, hi, Uf)) relative to the detector's integer part and the
+// fraction a = fma(m, hi, -cell) + fma(m, lo, Uf), bit-identical to the
+// adjoint's cell_rel / cell_frac.  The floor is taken by floor_biased, whose
+// result's bit pattern is the biased integer cell: it is clamped and turned
+// into a shared-memory byte offset with integer arithmetic only.
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -23,199 +44,182 @@ namespace patgpu {
 
 namespace {
 
-// One bilinear sample of the staged band, branch free: a sample whose cell
-// lies outside the band (it belongs to another band or to no pixel) reads the
-// zero 2 x 2 block at offset 1 of the band's left padding instead.  Cells are
-// relative to the detector's integer part (Ui, Vi); `base` is the offset of
-// cell (Ui, Vi) in the band, and the relative cell (iu, iv) is inside the band
-// iff iu - ul <= uw and iv - vl <= vw (unsigned).
+// Stages the coefficient cells of tile task sg (see the file comment) from
+// image fi (N x N, row-major) into cells (pitch sg.pitch).  A thread takes a
+// column of kStageRows cells: it issues the kStageRows + 1 rows' loads of its
+// two pixel columns at once (one round trip through L2), then forms the cells.
+constexpr int kStageRows = 8;
 template <typename T>
-__device__ __forceinline__ float sample(const T* __restrict__ s, int W, int base, float mf, float4 r, float Uf,
-                                        float Vf, int ul, unsigned uw, int vl, unsigned vw)
+__device__ __forceinline__ void stage_cells(float4* __restrict__ cells, const T* __restrict__ fi, int n,
+                                            const Segment& sg)
 {
-    const float fu = cell_rel(mf, r.x, Uf), fv = cell_rel(mf, r.y, Vf);
-    const int iu = __float2int_rz(fu), iv = __float2int_rz(fv);
-    const bool ok = ((unsigned)(iu - ul) <= uw) & ((unsigned)(iv - vl) <= vw);
-    const T* p = s + (ok ? iv * W + iu + base : 1);
+    const int SW = sg.x1 - sg.x0 + 3, SH = sg.y1 - sg.y0 + 3;
+    const int segs = SW * ((SH + kStageRows - 1) / kStageRows);
+    for (int idx = threadIdx.x; idx < segs; idx += blockDim.x) {
+        const int sgi = idx / SW, cc = idx - sgi * SW;
+        const int rb = sgi * kStageRows;
+        const int px = sg.x0 - 2 + cc;   // the cell's left pixel column
+        const bool okx0 = px >= sg.x0 && px < sg.x1, okx1 = px + 1 >= sg.x0 && px + 1 < sg.x1;
+        float v0[kStageRows + 1], v1[kStageRows + 1];
+#pragma unroll
+        for (int i = 0; i <= kStageRows; ++i) {
+            const int py = sg.y0 - 2 + rb + i;   // pixel row i of this column of cells
+            const bool oky = py >= sg.y0 && py < sg.y1;
+            const T* p = fi + (size_t)(oky ? py : sg.y0) * n;
+            v0[i] = (oky && okx0) ? ld_img(p + px) : 0.f;
+            v1[i] = (oky && okx1) ? ld_img(p + px + 1) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < kStageRows; ++i) {
+            if (rb + i >= SH) break;
+            const float cx = v1[i] - v0[i];
+            cells[(rb + i) * sg.pitch + cc] = make_float4(v0[i], cx, v0[i + 1] - v0[i], (v1[i + 1] - v0[i + 1]) - cx);
+        }
+    }
+}
+
+// Per-unit constants of the sample evaluation: clamp bounds of the biased
+// cell bits (floor_biased results) and the offset that turns the clamped
+// bits into a byte offset of the staged cell.
+struct UnitFrame {
+    uint32_t ulo, uhi, vlo, vhi, row_bytes, koff;
+};
+
+__device__ __forceinline__ UnitFrame unit_frame(const Segment& sg, const InstDev& in, float4 d)
+{
+    UnitFrame u;
+    const int Ui = __float2int_rz(d.x), Vi = __float2int_rz(d.y);
+    // staged column index = floor + Ui + c0 - (x0 - 2); bits = kMagicBits + floor
+    u.ulo = kMagicBits + (uint32_t)(sg.x0 - 2 - Ui - in.c0);
+    u.vlo = kMagicBits + (uint32_t)(sg.y0 - 2 - Vi - in.c0);
+    u.uhi = u.ulo + (uint32_t)(sg.x1 - sg.x0 + 2);
+    u.vhi = u.vlo + (uint32_t)(sg.y1 - sg.y0 + 2);
+    u.row_bytes = (uint32_t)sg.pitch * 16u;
+    u.koff = 0u - (u.vlo * u.row_bytes + u.ulo * 16u);   // modulo 2^32
+    return u;
+}
+
+// One sample (radius mf, ray r = (hi_u, hi_v, lo_u, lo_v)) of the staged tile.
+__device__ __forceinline__ float sample(const unsigned char* __restrict__ smem, const UnitFrame& u, float mf,
+                                        float4 r, float Uf, float Vf)
+{
+    const float tu = floor_biased(__fmaf_rn(mf, r.x, Uf));
+    const float tv = floor_biased(__fmaf_rn(mf, r.y, Vf));
+    const float fu = __fsub_rn(tu, kMagic), fv = __fsub_rn(tv, kMagic);
     const float a = cell_frac(mf, r.x, r.z, Uf, fu), b = cell_frac(mf, r.y, r.w, Vf, fv);
-    const float f00 = ld_img(p), f10 = ld_img(p + 1), f01 = ld_img(p + W), f11 = ld_img(p + W + 1);
-    const float top = fmaf(a, f10 - f00, f00);
-    const float bot = fmaf(a, f11 - f01, f01);
-    return fmaf(b, bot - top, top);
+    const uint32_t iu = min(max(__float_as_uint(tu), u.ulo), u.uhi);
+    const uint32_t iv = min(max(__float_as_uint(tv), u.vlo), u.vhi);
+    const float4 c = *reinterpret_cast<const float4*>(smem + (iv * u.row_bytes + iu * 16u + u.koff));
+    return fmaf(b, fmaf(a, c.w, c.z), fmaf(a, c.y, c.x));
 }
 
 } // namespace
 
 template <int ML, typename T>
-__global__ void __launch_bounds__(kCircThreads) k_circmean(DevPlan dp, const T* __restrict__ f)
+__global__ void __launch_bounds__(kCircThreads, 2) k_circmean(DevPlan dp, const T* __restrict__ f)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    T* s = reinterpret_cast<T*>(smem_raw);
+    __shared__ __align__(8) uint64_t bar[2];
+    float4* cells = reinterpret_cast<float4*>(smem_raw);
     float4* rays_s = reinterpret_cast<float4*>(smem_raw + dp.fwd_rays_off);
     constexpr int QL = kWarp / ML;
-    constexpr int CO = ImgTraits<T>::col_off;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ml = lane % ML, ql = lane / ML;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);   // the wait probe's barrier: nothing ever arrives on it
         fence_mbar_init();
     }
     __syncthreads();
-    pdl_wait();   // f and the work queues belong to earlier work in the stream
 
     uint32_t parity = 0;
     const int task_begin = dp.cta_seg[blockIdx.x], task_end = dp.cta_seg[blockIdx.x + 1];
     for (int tidx = task_begin; tidx < task_end; ++tidx) {
         const Segment sg = dp.segs[tidx];
         const InstDev in = dp.inst[sg.inst];
-        const int n = in.n;
-        const int W = ImgTraits<T>::pitch(n);
-        const int rows = sg.band_hi - sg.band_lo + 1;
-        const int nu = sg.unit_end - sg.unit_begin;
-        __syncthreads(); // every warp is done with the previous band
+        __syncthreads(); // every warp is done with the previous tile
 
-        // ---- stage the band's image rows (TMA bulk copies) -----------------
-        if (threadIdx.x < 32) {
-            const int r0 = max(sg.band_lo, 0), r1 = min(sg.band_hi, n - 1);
-            const uint32_t row_bytes = (uint32_t)n * sizeof(T);
+        // ---- the instance's rays (TMA bulk copy; a plan table, so before the
+        // dependency wait) and the tile's cells (from f, after it) -----------
+        if (threadIdx.x == 0) {
             const uint32_t ray_bytes = (uint32_t)in.K * (uint32_t)sizeof(float4);
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bar, (r1 >= r0 ? (uint32_t)(r1 - r0 + 1) * row_bytes : 0u) + ray_bytes);
-                bulk_g2s(rays_s, dp.rays + in.ray_off, ray_bytes, &bar);
-            }
-            __syncwarp();
-            for (int r = r0 + lane; r <= r1; r += 32)
-                bulk_g2s(s + (r - sg.band_lo) * W + CO, f + in.f_off + (size_t)r * n, row_bytes, &bar);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[0], ray_bytes);
+            bulk_g2s(rays_s, dp.rays + in.ray_off, ray_bytes, &bar[0]);
         }
-        // ---- zero borders: columns 0 .. CO-1 and N+CO .. W-1 (padding), rows
-        // outside the image; columns 1, 2 of rows 0, 1 are the zero block
-        const T zero = T(0.f);
-        const int pad = W - (CO + n);
-        for (int i = threadIdx.x; i < rows * (pad + CO); i += blockDim.x) {
-            const int ri = i / (pad + CO), c = i - ri * (pad + CO);
-            s[ri * W + (c < CO ? c : n + c)] = zero;
-        }
-        // only the first band row (-1) and the last (n) can lie outside the image
-        if (sg.band_lo < 0)
-            for (int c = threadIdx.x; c < n; c += blockDim.x) s[CO + c] = zero;
-        if (sg.band_hi >= n)
-            for (int c = threadIdx.x; c < n; c += blockDim.x) s[(n - sg.band_lo) * W + CO + c] = zero;
+        if (tidx == task_begin) pdl_wait();   // f belongs to earlier work in the stream
+        stage_cells(cells, f + in.f_off, in.n, sg);
         __syncthreads();
-        if (!mbar_wait_bounded(&bar, parity, dp.status, 1)) {
-            mbar_wait_bounded(&bar, parity, dp.status, 1); // let copies in flight land before exiting
+        if (!mbar_wait_bounded(&bar[0], parity, dp.status, 1)) {
+            mbar_wait_bounded(&bar[0], parity, dp.status, 1); // let copies in flight land before exiting
             return;
         }
         parity ^= 1u;
+        if (dp.wait_probe > 0 && blockIdx.x == 0 && tidx == task_begin) {
+            // test hook: a wait that runs out (no copy is in flight here)
+            if (!mbar_wait_bounded(&bar[1], 0, dp.status, 2, dp.wait_probe)) return;
+        }
 
-        // ---- units: shared queue of every CTA working on this band task ----
-        // centred cell (i0c, j0c) lives at s[(j0c + c0 - band_lo) * W + i0c + c0 + CO]
-        const int ulo = -1 - in.c0, vlo = sg.band_lo - in.c0;
-        const unsigned uw = (unsigned)n, vw = (unsigned)(sg.band_hi - 1 - sg.band_lo);
+        // ---- this warp's units (static schedule) ------------------------------
         const float4* det = dp.det + in.det_off;
-        const Unit* units = dp.units + sg.unit_begin;
-        int32_t* queue = dp.work_counters + (2 + sg.queue) * kQueueStride;
-
         const size_t plane = (size_t)in.n_det * in.n_r;
-        const int32_t* slotcnt = reinterpret_cast<const int32_t*>(dp.slotcnt + in.slotcnt_off);
-        // The last unit of (j, radius block) to arrive sums the block's slots in
-        // slot order (deterministic) into M and re-arms the counter.
-        // blocks are j * nmb + m0 / ML; this lane's radius in a block is m0 + ml
-        int p_blk = -1;                  // slot written, arrival not yet counted
-        int q_blk = -1, q_total = 0;     // arrival counted, result pending (lane 0)
-        int q_ret = 0;
-        auto resolve = [&]() {
-            const int last = __shfl_sync(0xffffffffu, q_ret == q_total - 1 ? 1 : 0, 0);
-            if (last) {
-                __threadfence();
-                const int q_j = q_blk / in.nmb, q_m = (q_blk - q_j * in.nmb) * ML + ml;
-                if (ql == 0 && q_m < in.n_r) {
-                    const float* sl0 = dp.mpart + in.mpart_off + (size_t)q_j * in.n_r + q_m;
-                    // four slots' loads in flight at a time, added in slot order
-                    float sum = 0.f;
-                    int sl = 0;
-                    for (; sl + 4 <= q_total; sl += 4) {
-                        const float a0 = __ldcg(sl0 + (size_t)sl * plane), a1 = __ldcg(sl0 + (size_t)(sl + 1) * plane);
-                        const float a2 = __ldcg(sl0 + (size_t)(sl + 2) * plane), a3 = __ldcg(sl0 + (size_t)(sl + 3) * plane);
-                        sum += a0;
-                        sum += a1;
-                        sum += a2;
-                        sum += a3;
-                    }
-                    for (; sl < q_total; ++sl) sum += __ldcg(sl0 + (size_t)sl * plane);
-                    dp.msum[in.mbar_off + (size_t)q_j * in.n_rp + q_m] = sum;
-                }
-                if (lane == 0) dp.slot_arrivals[in.arrive_off + q_blk] = 0;
-            }
-            q_blk = -1;
-        };
-
-        int u = 0;
-        if (lane == 0) u = atomicAdd(queue, 1);
-        u = __shfl_sync(0xffffffffu, u, 0);
+        float* mpart = dp.mpart + in.mpart_off;
+        const int ub = dp.warp_units[sg.warp_off + warp], ue = dp.warp_units[sg.warp_off + warp + 1];
         Unit un{};
-        if (u < nu) un = units[u];
-        while (u < nu) {
-            // take and fetch the next unit while this one is processed
-            int u2 = 0;
-            if (lane == 0) u2 = atomicAdd(queue, 1);
-            u2 = __shfl_sync(0xffffffffu, u2, 0);
+        if (ub < ue) un = dp.units[ub];
+        for (int ui = ub; ui < ue; ++ui) {
             Unit un2{};
-            if (u2 < nu) un2 = units[u2];
-
+            if (ui + 1 < ue) un2 = dp.units[ui + 1];   // the next unit's record, in flight meanwhile
             const int m = un.m0 + ml;
             const float mf = (float)m;
             const float4 d = __ldg(det + un.j);
-            const int Ui = __float2int_rz(d.x), Vi = __float2int_rz(d.y);
-            const int base = (Vi + in.c0 - sg.band_lo) * W + Ui + in.c0 + CO;
-            const int ul = ulo - Ui, vl = vlo - Vi;
+            const UnitFrame fr = unit_frame(sg, in, d);
             const float4* tq = rays_s + un.q0 + ql;   // units never wrap past K
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
             int i = ql;
             for (; i + 3 * QL < un.nq; i += 4 * QL, tq += 4 * QL) {
                 const float4 c0 = tq[0], c1 = tq[QL], c2 = tq[2 * QL], c3 = tq[3 * QL];
-                acc0 += sample(s, W, base, mf, c0, d.z, d.w, ul, uw, vl, vw);
-                acc1 += sample(s, W, base, mf, c1, d.z, d.w, ul, uw, vl, vw);
-                acc2 += sample(s, W, base, mf, c2, d.z, d.w, ul, uw, vl, vw);
-                acc3 += sample(s, W, base, mf, c3, d.z, d.w, ul, uw, vl, vw);
+                acc0 += sample(smem_raw, fr, mf, c0, d.z, d.w);
+                acc1 += sample(smem_raw, fr, mf, c1, d.z, d.w);
+                acc2 += sample(smem_raw, fr, mf, c2, d.z, d.w);
+                acc3 += sample(smem_raw, fr, mf, c3, d.z, d.w);
             }
-            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(s, W, base, mf, *tq, d.z, d.w, ul, uw, vl, vw);
+            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(smem_raw, fr, mf, *tq, d.z, d.w);
             float acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
             for (int o = ML; o < kWarp; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            // Pipelined arrival: the arrival counted for the unit before last
-            // is resolved now (its atomic returned while this unit was sampled),
-            // the previous unit's arrival is issued now (its slot write has
-            // drained, so the fence is cheap), and this unit's slot is written.
-            if (q_blk >= 0) resolve();
-            if (p_blk >= 0) {
-                __threadfence();
-                q_blk = p_blk;
-                q_total = slotcnt[p_blk];
-                if (lane == 0) q_ret = atomicAdd(dp.slot_arrivals + in.arrive_off + p_blk, 1);
-            }
-            if (ql == 0 && m < in.n_r) dp.mpart[in.mpart_off + (size_t)un.slot * plane + (size_t)un.j * in.n_r + m] = acc;
-            p_blk = un.j * in.nmb + un.m0 / ML;
-            u = u2;
+            if (ql == 0 && m < in.n_r) mpart[(size_t)un.slot * plane + (size_t)un.j * in.n_r + m] = acc;
             un = un2;
         }
-        if (q_blk >= 0) resolve();
-        if (p_blk >= 0) {
-            __threadfence();
-            q_blk = p_blk;
-            q_total = slotcnt[p_blk];
-            if (lane == 0) q_ret = atomicAdd(dp.slot_arrivals + in.arrive_off + p_blk, 1);
-            resolve();
-        }
-        // this CTA is done with the band task; its last participant re-arms the queue
-        __syncthreads();
-        if (threadIdx.x == 0 && atomicAdd(queue + 1, 1) == sg.parts - 1) {
-            queue[0] = 0;
-            queue[1] = 0;
-        }
     }
+}
+
+// M[j][m] = sum over the slots of (j, m / ML) in slot order.  Grid (rows of
+// M, radius chunks of 128); a row is an (instance, detector) pair.
+// A thread keeps eight slots' loads in flight and adds them in slot order.
+__global__ void __launch_bounds__(128) k_msum(DevPlan dp)
+{
+    const int2 row = dp.msum_rows[blockIdx.x];
+    const InstDev in = dp.inst[row.x];
+    const int j = row.y;
+    const int m = blockIdx.y * blockDim.x + threadIdx.x;
+    if (m >= in.n_r) return;
+    const int cnt = __ldg(reinterpret_cast<const int32_t*>(dp.slotcnt + in.slotcnt_off) + (size_t)j * in.nmb +
+                          m / dp.m_lanes);
+    const size_t plane = (size_t)in.n_det * in.n_r;
+    const float* src = dp.mpart + in.mpart_off + (size_t)j * in.n_r + m;
+    pdl_wait();   // the partial slots come from the circular-mean kernel
+    float s = 0.f;
+    for (int sl = 0; sl < cnt; sl += 8) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = sl + k < cnt ? __ldcg(src + (size_t)(sl + k) * plane) : 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (sl + k < cnt) s += v[k];
+    }
+    dp.msum[in.mbar_off + (size_t)j * in.m_pitch + m] = s;
 }
 
 // Samples whose cell touches the grid, counted with the kernels' FP32 arithmetic.
@@ -274,7 +278,10 @@ cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st)
     DevPlan copy = dp;
     const void* fptr = f;
     void* args[] = {&copy, &fptr};
-    return cudaLaunchKernelExC(&cfg, fn, args);
+    e = cudaLaunchKernelExC(&cfg, fn, args);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_msum, dim3((unsigned)dp.n_msum_rows, (unsigned)((dp.n_r_max + 127) / 128)), dim3(128), 0, st,
+                      1, dp);
 }
 
 int circmean_blocks_per_sm(int m_lanes, bool bf16, int smem_bytes)

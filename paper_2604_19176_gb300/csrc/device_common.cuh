@@ -1,5 +1,5 @@
 // device_common.cuh — small device helpers shared by the kernels of this
-// library (shared-memory band layout, TMA bulk copies with mbarriers,
+// library (split-form sample coordinates, TMA bulk copies with mbarriers,
 // bounded waits, reductions, the polynomial atan2 of the adjoint window).
 #pragma once
 
@@ -13,27 +13,6 @@ namespace patgpu {
 
 __device__ __forceinline__ float ld_img(const float* p) { return *p; }
 __device__ __forceinline__ float ld_img(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-
-__device__ __forceinline__ int pitch_f32(int n)
-{
-    int w = n + kColOff + 1;
-    return w + ((12 - (w & 31)) & 31);
-}
-__device__ __forceinline__ int pitch_bf16(int n)
-{
-    int w = n + kColOffBF16 + 1;
-    return w + ((24 - (w & 63)) & 63);
-}
-
-template <typename T> struct ImgTraits;
-template <> struct ImgTraits<float> {
-    static __device__ __forceinline__ int pitch(int n) { return pitch_f32(n); }
-    static constexpr int col_off = kColOff;
-};
-template <> struct ImgTraits<__nv_bfloat16> {
-    static __device__ __forceinline__ int pitch(int n) { return pitch_bf16(n); }
-    static constexpr int col_off = kColOffBF16;
-};
 
 // ---------------------------------------------------------------------------
 // Sample coordinates in split form (the coordinate conventions of
@@ -50,6 +29,15 @@ __device__ __forceinline__ float cell_frac(float mf, float hi, float lo, float f
 {
     return __fadd_rn(__fmaf_rn(mf, hi, -cell), __fmaf_rn(mf, lo, f0));
 }
+
+// Floor of x (|x| < 2^22) by one directed-rounding add: x + 1.5 * 2^23
+// rounded toward -inf is floor(x) + 1.5 * 2^23 exactly (the sum's ulp is 1),
+// so the returned float's bit pattern is kMagicBits + floor(x) and
+// floor(x) = result - kMagic.  The ordinary FP32 pipe does this; floorf and
+// float->int conversions go through the slower conversion unit.
+constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;
+__device__ __forceinline__ float floor_biased(float x) { return __fadd_rd(x, kMagic); }
 
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch.  Kernels of the operator chain are launched
@@ -164,6 +152,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         }
     }
     return true;
+}
+
+// Bulk prefetch of [src, src + bytes) into L2 (src 16-byte aligned, bytes a
+// multiple of 16); no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // 16-byte asynchronous global -> shared copy (L2 only), and its completion.

@@ -77,11 +77,11 @@ int adj_cells_blocks_per_sm();
 int adj_list_blocks_per_sm(bool frac);
 
 // Adjoint list building at plan creation: counts the hits of every cell of
-// instance inst_idx into `counts` (out == nullptr), or, given those counts
-// and the instance's (patch, part) block bases `pbase` (16-byte units), fills
-// the interleaved lists as packed codes (4 B per sample) or fraction lists
-// (frac: 12 B per sample).
-cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
-                             uint32_t* out, bool frac, cudaStream_t st);
+// instance inst_idx into `counts` (out == nullptr), or, given the cells'
+// padded list starts `start` (entries), fills the lists as packed codes
+// (4 B per entry) or, with fa / fb, as weight indices plus the fractions
+// a, b (12 B per entry).
+cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* start,
+                             uint32_t* out, float* fa, float* fb, cudaStream_t st);
 
 } // namespace patgpu

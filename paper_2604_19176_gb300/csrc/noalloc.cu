@@ -15,7 +15,9 @@
 // before any stream capture.  All calls share the array: calls whose work
 // overlaps on the GPU (different streams, no ordering) race on it.  Every call
 // writes each scratch entry it later reads, so nothing has to start at zero.
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "device_common.cuh"
@@ -75,13 +77,23 @@ __global__ void __launch_bounds__(256) k_tv_noalloc(const float* __restrict__ f,
     }
 }
 
-// value[img] = sum of the image's tile partials, in tile order.
+// value[img] = sum of the image's tile partials.  One warp per image: lane l
+// adds tiles l, l + 32, l + 64, ... in order, then the 32 lane sums are added
+// by a fixed shuffle tree, so the result is the same on every call.
 __global__ void k_tv_noalloc_sum(const float* __restrict__ partial, int tiles_img, float* __restrict__ value)
 {
-    if (threadIdx.x != 0) return;
+    const float* p = partial + (size_t)blockIdx.x * tiles_img;
     float s = 0.f;
-    for (int t = 0; t < tiles_img; ++t) s += partial[(size_t)blockIdx.x * tiles_img + t];
-    value[blockIdx.x] = s;
+    for (int t = threadIdx.x; t < tiles_img; t += 32) s += p[t];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) value[blockIdx.x] = s;
+}
+
+// true when the byte ranges [a, a + na) and [b, b + nb) overlap
+bool overlaps(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
 }
 
 // Device address of g_tv_scratch on the current device, looked up once per device.
@@ -119,7 +131,17 @@ extern "C" pat_status_t pat_tv_grad_noalloc(const float* d_f, int32_t n, int32_t
     const int tiles_x = (n + 31) / 32, tiles_y = (n + 7) / 8;
     const int64_t tiles_img = (int64_t)tiles_x * tiles_y;
     const int64_t tiles = tiles_img * batch;
-    if (tiles > PAT_TV_NOALLOC_MAX_TILES) return PAT_ERR_INVALID_ARG; // beyond the fixed scratch
+    if (tiles > INT32_MAX) return PAT_ERR_INVALID_ARG;
+    // The stencil reads neighbours that other CTAs may already have written:
+    // the gradient must not overlap the images, nor the values either of them.
+    const size_t img_bytes = sizeof(float) * (size_t)n * (size_t)n * (size_t)batch;
+    if (d_grad && overlaps(d_f, img_bytes, d_grad, img_bytes)) return PAT_ERR_INVALID_ARG;
+    if (d_value) {
+        const size_t vb = sizeof(float) * (size_t)batch;
+        if (overlaps(d_f, img_bytes, d_value, vb) || (d_grad && overlaps(d_grad, img_bytes, d_value, vb)))
+            return PAT_ERR_INVALID_ARG;
+        if (tiles > PAT_TV_NOALLOC_MAX_TILES) return PAT_ERR_INVALID_ARG; // beyond the fixed scratch
+    }
     float* scratch = nullptr;
     if (d_value) {
         const pat_status_t s = scratch_address(&scratch);

@@ -35,15 +35,12 @@
 namespace patgpu {
 
 constexpr int kWarp = 32;
-constexpr int kColOff = 4;        // FP32 shared image: column 0 at word offset 4 (16 B aligned)
-constexpr int kColOffBF16 = 8;    // BF16 shared image: column 0 at element offset 8 (16 B aligned)
 constexpr int kPatchW = 8;        // adjoint: one warp owns an 8 x 4 patch of cells
 constexpr int kPatchH = 4;
 // Work queues live kQueueStride ints apart (one 128-byte line each, so that
 // queues taken by different CTAs do not serialise on one L2 line): queue 0 is
-// the adjoint cell kernel's, queue 1 the adjoint list kernel's, queue 2 + t
-// circular-mean band task t's.  Each queue is two ints: the next item and the
-// count of finished participants.
+// the adjoint cell kernel's, queue 1 the adjoint list kernel's.  Each queue
+// is two ints: the next item and the count of finished participants.
 constexpr int kQueueStride = 32;
 
 // Per-instance descriptor (device resident, read by every kernel).
@@ -55,39 +52,41 @@ struct InstDev {
     int32_t n_slots, nmb;          // forward partial slots; radius blocks per detector
     int64_t f_off, g_off;          // element offsets of the instance's image / data
     int64_t mpart_off;             // float offset of forward partial slots (n_slots x n_det x n_r)
-    int64_t mbar_off;              // float offset of M and of Mbar (n_det rows of pitch n_rp)
+    int64_t mbar_off;              // float offset of M and of Mbar (n_det rows of pitch m_pitch)
     int64_t p_off;                 // float offset of P (n_t rows, pitch n_rp), then P^T (n_r rows, pitch n_tp)
     int64_t slotcnt_off;           // byte offset of the slot counts (n_det x nmb int32)
     int64_t z_off;                 // float4 offset of the adjoint cell sums (groups x (n+1)^2)
     int64_t ray_off;               // entry offset of the instance's 2K rays and reciprocal rays
-    int64_t arrive_off;            // int offset of the slot-arrival counters (n_det x nmb)
-    int64_t list_off;              // adjoint lists: offset of the instance's (n+1)^2 cell counts
-    int32_t code_qbits, code_mbits; // adjoint list mode: code = j << (qb+mb) | m << qb | q
-    int32_t n_rp;                  // row pitch (multiple of 32) of M, Mbar and P
+    int64_t list_off;              // adjoint lists: offset of the instance's (n+1)^2 + 1 cell starts
+    int32_t code_jbits, code_mbits; // adjoint list mode: code = q << (jb+mb) | j << mb | m
+    int32_t n_rp;                  // row pitch (multiple of 32) of P
     int32_t n_tp;                  // row pitch (multiple of 32) of P^T
-    int32_t patches_x;             // 8 x 4 cell patches per row of patches: ceil((n+1)/8)
-    int64_t pbase_off;             // adjoint lists: offset of the instance's (patch, part) list bases
+    int32_t m_pitch;               // row pitch of M and Mbar: a power of two > n_r (the columns from
+                                   //   n_r on stay zero), so a list code's low bits are j * m_pitch + m
+    int32_t pad2;
 };
 
 // Circular-mean work unit: radii [m0, m0 + m_lanes) of detector j, angles
-// q0 .. q0 + nq - 1 (mod K), restricted to one image band; its partial sums
-// go to forward slot `slot`.  32 bytes so that a segment's units can be
-// bulk-copied to shared memory.
+// q0 .. q0 + nq - 1 (never past K), restricted to one tile; its partial sums
+// go to forward slot `slot` (the slots of a (detector, radius block) are
+// added in slot order by k_msum).  32 bytes.
 struct Unit {
     int32_t j, m0, q0, nq, slot, pad[3];
 };
 
-// Band task of the circular means: the units [unit_begin, unit_end) of one
-// (instance, band), taken from a global queue by the `parts` CTAs that stage
-// this band of the image in shared memory.
+// Tile task of the circular means: the pixels [x0, x1) x [y0, y1) of one
+// instance (tiles partition every image), processed by one CTA.  The staged
+// cells are [x0 - 2, x1] x [y0 - 2, y1] (cell (c, r) spans pixels c..c+1,
+// r..r+1; pixels outside the tile count as zero), `pitch` cells per row.
+// Warp w of the CTA processes units[warp_units[warp_off + w] ..
+// warp_units[warp_off + w + 1]) (a static schedule, balanced at plan time).
 struct Segment {
     int32_t inst;
-    int32_t band_lo;   // first cell row of the band (absolute, may be -1)
-    int32_t band_hi;   // one past the last cell row (absolute, <= N)
-    int32_t unit_begin, unit_end;
-    int32_t queue;     // index of the task's queue counters
-    int32_t parts;     // CTAs working on the task
-    int32_t pad;
+    int32_t x0, x1;    // owned pixel columns
+    int32_t y0, y1;    // owned pixel rows
+    int32_t pitch;     // staged cells per row (>= x1 - x0 + 3)
+    int32_t warp_off;  // index of this task's first per-warp offset
+    int32_t pad[5];
 };
 
 // Output tile of the two Abel (time) stages: detectors [j0, j0 + kAbelJ),
@@ -96,11 +95,18 @@ struct TimeTile {
     int32_t inst, j0, x0, pad;
 };
 
-// Adjoint cell item: the 8 x 4 patch of cells with lower-left cell (x0, y0)
-// (absolute indices, >= -1) of instance inst, for detectors j = group (mod G).
+// Adjoint cell item of instance inst: in enumeration mode the 8 x 4 patch of
+// cells with lower-left cell (x0, y0) (absolute indices, >= -1) for detectors
+// j = group (mod G); in list mode the 2 x 2 block of cells at (x0, y0).
 struct CellItem {
     int32_t inst, x0, y0, group;
 };
+
+// Adjoint lists.  Cell c of an instance (cells numbered (cy + 1) * (n + 1) +
+// cx + 1) owns entries [start[c], start[c + 1]) of the list arrays: its
+// samples in the order (j, q, m), padded with null entries (weight index of
+// the always-zero column m_pitch - 1 of row 0) to a multiple of kListPad.
+constexpr int kListPad = 8;        // lanes per cell in the list gather
 
 // Tile of the elementwise / stencil kernels: 32 x 8 pixels.
 struct ImgTile {
@@ -115,20 +121,22 @@ struct DevPlan {
     const float2* rtrig;           // (1/dcos hi, 1/dsin hi), 2K entries per instance
     const float* P;                // Abel matrices P then P^T, per distinct n_t
     const uint8_t* slotcnt;        // forward slots per (detector, radius block), int32
-    const Unit* units;
+    const Unit* units;             // circular-mean units, grouped by (tile task, warp)
+    const int32_t* warp_units;     // per (tile task, warp): first unit (see Segment)
     const Segment* segs;
     const int32_t* cta_seg;        // CTA c processes segments [cta_seg[c], cta_seg[c+1])
+    const int2* msum_rows;         // (instance, detector) of every row of M, for k_msum
     const TimeTile* fwd_tiles;
     const TimeTile* adj_tiles;
     const CellItem* cell_items;
     const ImgTile* img_tiles;
-    const int64_t* list_base;      // adjoint lists: first 16-byte vector of each (patch, part) block
-    const int32_t* cell_cnt;       // adjoint lists: number of hits of each cell
-    const uint32_t* codes;         // adjoint lists: packed (j, m, q) codes, or 48-byte fraction vectors
-    const CellItem* list_items;    // adjoint list mode: (patch, part) items, longest parts first
+    const int64_t* cell_start;     // adjoint lists: first entry of each cell (see kListPad)
+    const uint32_t* codes;         // adjoint lists: packed (q, j, m) codes, or weight indices j * m_pitch + m
+    const float* frac_a;           // fraction lists: the FP32 fractions a, b of every entry
+    const float* frac_b;
+    const CellItem* list_items;    // adjoint list mode: 2 x 2 cell blocks, longest lists first
     float* mpart;                  // forward partial slots
     float* msum;                   // forward circular-mean sums M (same layout as Mbar)
-    int32_t* slot_arrivals;        // per (detector, radius block): units finished this call
     int32_t* work_counters;        // dynamic work queues, kQueueStride ints apart (see kQueueStride)
     float* mbar;                   // adjoint Mbar
     float4* zbuf;                  // adjoint per-group cell sums
@@ -136,11 +144,15 @@ struct DevPlan {
     int32_t* status;               // device status word (bounded waits)
     int32_t n_inst;
     int32_t n_fwd_ctas, n_fwd_tiles, n_adj_tiles, n_cell_items, n_img_tiles, n_list_items;
+    int32_t n_msum_rows;           // rows of M over all instances
+    int32_t n_r_max;               // largest n_r of any instance
     int32_t m_lanes, adj_groups;
     int32_t adj_mode;              // 3 = fraction lists, 1 = code lists, 0 = compute mode
     int32_t cell_blocks;           // CTAs of the adjoint cell kernel (8 warps each)
     int32_t fwd_smem_bytes;        // dynamic shared memory of the circular-mean kernel
-    int32_t fwd_rays_off;          // byte offset of the staged rays (after the largest band)
+    int32_t fwd_rays_off;          // byte offset of the staged rays (after the largest tile)
+    int32_t wait_probe;            // test hook: CTA 0 of the next circular-mean launch waits on a
+                                   //   barrier nothing completes (bounded by wait_probe clocks)
     int32_t abel_cluster_fwd;      // CTAs per cluster splitting each forward time contraction
     int32_t abel_cluster_adj;      // the same for the adjoint time contraction
     int32_t bf16;                  // image storage is BF16
@@ -151,21 +163,15 @@ constexpr int kAbelX = 32;         // outputs per Abel tile (one per lane)
 constexpr int kAbelWarps = 8;      // warps per Abel CTA
 constexpr int kAbelKC = 32;        // contraction rows staged per pipeline stage
 
-// Shared-memory row pitch (elements) of a band of an N-wide image.  The
-// pitch leaves a zero column on each side, keeps rows 16-byte aligned, and is
-// congruent to 12 (FP32 words) mod 32 so that the 2 x 2 texel reads of 32
-// lanes walking along a ray spread over the 32 banks.
-inline int band_pitch_f32(int n)
+// Staged cells per row of a circular-mean tile `w` pixels wide: w + 3 cells,
+// padded to 5 mod 8.  A cell is 16 bytes (4 banks); eight lanes reading the
+// cells along a 4-pixel stretch of a ray then fall into distinct bank groups
+// except for offsets (+-3, -+1)-like pairs (v * pitch + u = 0 mod 8).
+inline int cell_pitch(int w)
 {
-    int w = n + kColOff + 1;
-    while (w % 32 != 12) ++w;
-    return w;
-}
-inline int band_pitch_bf16(int n)
-{
-    int w = n + kColOffBF16 + 1;   // elements; words = w / 2
-    while (w % 64 != 24) ++w;
-    return w;
+    int p = w + 3;
+    while (p % 8 != 5) ++p;
+    return p;
 }
 
 } // namespace patgpu

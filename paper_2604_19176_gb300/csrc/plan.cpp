@@ -135,60 +135,68 @@ std::vector<float> build_abel_matrix_uncached(int n_t)
 }
 
 struct GeomKey {
-    int n, n_det, n_t, K, bf16, ml, qp, rows;
+    int n, n_det, n_t, K, ml, qp, tw, th;
     double a0, span, tmax;
     bool operator<(const GeomKey& o) const
     {
-        return std::tie(n, n_det, n_t, K, bf16, ml, qp, rows, a0, span, tmax) <
-               std::tie(o.n, o.n_det, o.n_t, o.K, o.bf16, o.ml, o.qp, o.rows, o.a0, o.span, o.tmax);
+        return std::tie(n, n_det, n_t, K, ml, qp, tw, th, a0, span, tmax) <
+               std::tie(o.n, o.n_det, o.n_t, o.K, o.ml, o.qp, o.tw, o.th, o.a0, o.span, o.tmax);
     }
 };
 
-struct BandTemplate {
-    int lo, hi;                      // cell rows [lo, hi)
-    std::vector<Unit> units;         // the band's units, largest first
+struct TileTemplate {
+    int x0, x1, y0, y1;              // owned pixels [x0, x1) x [y0, y1)
+    std::vector<Unit> units;         // the tile's units, largest first
     double cost = 0.0;
 };
 
 struct GeomTemplate {
-    std::vector<BandTemplate> bands;
+    std::vector<TileTemplate> tiles;
     std::vector<int32_t> slotcnt;    // n_det x nmb
     int n_slots = 0;
     int nmb = 0;
-    std::vector<int64_t> band_unit_base; // offset of each band's units in the global unit array
     int64_t slot_samples = 0;        // lane-samples the circular-mean kernel evaluates
 };
 
 constexpr double kUnitOverhead = 24.0; // per-unit fixed cost, in angle iterations
 
-// Angular chunks (of `G` consecutive q) whose annular sector (radii
-// [rlo, rhi] about (U, V)) can reach the rectangle [x0, x1] x [y0, y1]:
-// conservative test on the sector's bounding box.
-void mark_chunks(double U, double V, double rlo, double rhi, double x0, double x1, double y0, double y1, int K,
-                 int G, std::vector<uint8_t>& mark)
+// n pixels split into parts of at most w pixels, as equal as possible.
+std::vector<int> tile_edges(int n, int w)
 {
-    const int nch = (K + G - 1) / G;
-    mark.assign(nch, 0);
-    // quick reject: the annulus misses the rectangle entirely
-    const double cx = std::min(std::max(U, x0), x1), cy = std::min(std::max(V, y0), y1);
-    const double dmin = std::hypot(cx - U, cy - V);
-    const double fx = std::max(std::fabs(x0 - U), std::fabs(x1 - U));
-    const double fy = std::max(std::fabs(y0 - V), std::fabs(y1 - V));
-    const double dmax = std::hypot(fx, fy);
-    if (rhi < dmin || rlo > dmax) return;
-    const double pi = kTwoPi / 2;
-    for (int c = 0; c < nch; ++c) {
-        const int qa = c * G, qb = std::min((c + 1) * G, K) - 1;
-        const double pa = kTwoPi * qa / K, pb = kTwoPi * qb / K;
-        double cmin = std::min(std::cos(pa), std::cos(pb)), cmax = std::max(std::cos(pa), std::cos(pb));
-        double smin = std::min(std::sin(pa), std::sin(pb)), smax = std::max(std::sin(pa), std::sin(pb));
-        if (pa <= pi && pi <= pb) cmin = -1.0;
-        if (pa <= 0.5 * pi && 0.5 * pi <= pb) smax = 1.0;
-        if (pa <= 1.5 * pi && 1.5 * pi <= pb) smin = -1.0;
-        if (pa == 0.0) cmax = 1.0;
-        const double bx0 = U + std::min(rlo * cmin, rhi * cmin), bx1 = U + std::max(rlo * cmax, rhi * cmax);
-        const double by0 = V + std::min(rlo * smin, rhi * smin), by1 = V + std::max(rlo * smax, rhi * smax);
-        if (bx1 >= x0 && bx0 <= x1 && by1 >= y0 && by0 <= y1) mark[c] = 1;
+    const int parts = std::max(1, (n + w - 1) / w);
+    std::vector<int> e(parts + 1);
+    for (int i = 0; i <= parts; ++i) e[i] = (int)(((int64_t)i * n) / parts);
+    return e;
+}
+
+// Staged cells of a tile tw x th pixels (cell_pitch(tw) per row, th + 3 rows).
+int64_t tile_cells(int tw, int th) { return (int64_t)cell_pitch(tw) * (th + 3); }
+
+// Tile shape (pixel columns tw, rows th) of an n x n image when a tile may
+// stage `cells` cells: the split with the fewest tiles along x plus along y
+// (the least tile-edge length, where units straddling an edge are evaluated
+// on both sides), wider tiles on ties.  want_w / want_h > 0 fix a side.
+void choose_tile(int n, int64_t cells, int want_w, int want_h, int& tw, int& th)
+{
+    int best = 1 << 30;
+    tw = th = 0;
+    for (int tx = 1; tx <= n; ++tx) {
+        const int w = want_w > 0 ? std::min(want_w, n) : (n + tx - 1) / tx;
+        if (want_w > 0 && tx > 1) break;
+        int h = want_h > 0 ? std::min(want_h, n) : (int)std::min<int64_t>(n, cells / cell_pitch(w) - 3);
+        if (h < 1) continue;
+        if (want_h == 0 && tile_cells(w, h) > cells) continue;
+        const int ntx = (n + w - 1) / w, nty = (n + h - 1) / h;
+        if (ntx + nty < best) {
+            best = ntx + nty;
+            tw = w;
+            th = h;
+        }
+        if (w <= 8) break;
+    }
+    if (tw == 0) {   // nothing fits the budget: smallest tiles (the caller checks the shared memory)
+        tw = want_w > 0 ? std::min(want_w, n) : std::min(n, 8);
+        th = want_h > 0 ? std::min(want_h, n) : std::min(n, 8);
     }
 }
 
@@ -206,8 +214,6 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const bool bf16 = opt.image_dtype == PAT_BF16;
     const int ml = opt.m_lanes;
     const int qpiece = opt.q_piece;
-    const int esize = bf16 ? 2 : 4;
-    const int G = 4; // angle chunk of the unit builder
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PAT_ERR_CUDA;
@@ -246,7 +252,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         }
     }
 
-    // ---- per-geometry templates (units, bands, slots) ---------------------
+    // ---- per-geometry templates (tiles, units, slots) ----------------------
     std::map<GeomKey, int> tmpl_index;
     std::vector<GeomTemplate> tmpls;
     std::vector<int> inst_tmpl(n_inst);
@@ -254,22 +260,22 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     std::vector<float4> det4, rays;
     std::vector<float2> rtrig;
     std::vector<InstDev> inst(n_inst);
-    int band_bytes = 0;
-    int bands_max = 0;
+    int64_t tile_bytes = 0;
+    int tiles_max = 0;
     int K_max = 0;
     for (int i = 0; i < n_inst; ++i) K_max = std::max(K_max, geoms[i].n_angles);
-    const int ray_bytes = K_max * (int)sizeof(float4);   // staged beside the band
+    const int ray_bytes = K_max * (int)sizeof(float4);   // staged beside the tile
+    const int64_t cell_budget = std::max<int64_t>(P.band_budget_bytes - ray_bytes, 16 * 1024) / 16;
+    const int QL = kWarp / ml;
 
     for (int i = 0; i < n_inst; ++i) {
         const pat_geometry_t& g = geoms[i];
         const int n = g.n;
-        const int W = bf16 ? band_pitch_bf16(n) : band_pitch_f32(n);
-        int rows_max = opt.band_rows > 0 ? opt.band_rows
-                                         : (std::max(P.band_budget_bytes - ray_bytes, 16 * 1024) / (W * esize));
-        rows_max = std::max(rows_max, 3);
-        rows_max = std::min(rows_max, n + 2);
-        const int nb = (n + 1 + (rows_max - 1) - 1) / (rows_max - 1);
-        bands_max = std::max(bands_max, nb);
+        int tw = 0, th = 0;
+        choose_tile(n, cell_budget, opt.tile_cols, opt.band_rows, tw, th);
+        const std::vector<int> ex = tile_edges(n, tw), ey = tile_edges(n, th);
+        const int ntx = (int)ex.size() - 1, nty = (int)ey.size() - 1;
+        tiles_max = std::max(tiles_max, ntx * nty);
 
         InstDev& d = inst[i];
         std::memset(&d, 0, sizeof(d));
@@ -302,12 +308,13 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             const double ui = std::floor((double)uf), vi = std::floor((double)vf);
             det4.push_back(make_float4((float)ui, (float)vi, (float)(ue - ui), (float)(ve - vi)));
         }
-        // reciprocal ray slopes for the adjoint's slab test, from the FP32 table values
+        // M / Mbar row pitch and the adjoint list code q << (jb + mb) | j << mb | m
         {
             auto bits = [](int64_t v) { int b = 0; while ((1ll << b) < v) ++b; return std::max(b, 1); };
-            d.code_qbits = bits(g.n_angles);
-            d.code_mbits = bits(d.n_r);
-            P.code_bits_max = std::max(P.code_bits_max, d.code_qbits + d.code_mbits + bits(g.n_det));
+            d.code_mbits = bits(d.n_r + 1);      // m_pitch > n_r: column m_pitch - 1 stays zero
+            d.m_pitch = 1 << d.code_mbits;
+            d.code_jbits = bits(g.n_det);
+            P.code_bits_max = std::max(P.code_bits_max, bits(g.n_angles) + d.code_jbits + d.code_mbits);
         }
         // rays: delta (cos, sin)(2 pi q / K) as FP32 hi + lo pairs (2K entries so
         // that angle windows may run past K), and 1/hi for the adjoint's slab test
@@ -327,8 +334,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             }
         }
 
-        GeomKey key{n, g.n_det, g.n_t, g.n_angles, bf16 ? 1 : 0, ml, qpiece, rows_max, g.arc_start, g.arc_span,
-                    g.t_max};
+        GeomKey key{n, g.n_det, g.n_t, g.n_angles, ml, qpiece, tw, th, g.arc_start, g.arc_span, g.t_max};
         auto it = tmpl_index.find(key);
         if (it != tmpl_index.end()) {
             inst_tmpl[i] = it->second;
@@ -340,49 +346,81 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         tmpls.emplace_back();
         GeomTemplate& T = tmpls.back();
         T.nmb = d.nmb;
-        T.bands.resize(nb);
-        for (int b = 0; b < nb; ++b) {
-            T.bands[b].lo = -1 + (int)(((int64_t)b * (n + 1)) / nb);
-            T.bands[b].hi = -1 + (int)(((int64_t)(b + 1) * (n + 1)) / nb);
-            const int rows = T.bands[b].hi - T.bands[b].lo + 1;
-            band_bytes = std::max(band_bytes, rows * W * esize);
-        }
-        // Units: for every (band, detector, radius block) the angle chunks
-        // whose sector can reach the band's cells, split into pieces.
+        const int ntiles = ntx * nty;
+        T.tiles.resize(ntiles);
+        for (int ty = 0; ty < nty; ++ty)
+            for (int tx = 0; tx < ntx; ++tx) {
+                TileTemplate& tt = T.tiles[ty * ntx + tx];
+                tt.x0 = ex[tx];
+                tt.x1 = ex[tx + 1];
+                tt.y0 = ey[ty];
+                tt.y1 = ey[ty + 1];
+                tile_bytes = std::max<int64_t>(tile_bytes, 16 * tile_cells(tt.x1 - tt.x0, tt.y1 - tt.y0));
+            }
+        // Units.  A sample touches tile [x0, x1) x [y0, y1) iff its cell does,
+        // i.e. its centred position lies in [x0 - 1 - c0, x1 - c0) x
+        // [y0 - 1 - c0, y1 - c0).  For every (detector, radius block, ray) the
+        // block's samples lie on one straight segment, so the segment's
+        // bounding box (widened by eps, far above the FP32 position error)
+        // against those rectangles finds every tile a sample of it can touch.
+        // Runs of consecutive rays touching a tile become that tile's units.
         const int c0 = n / 2;
         const double eps = 0.01;
         const int K = g.n_angles;
-        std::vector<std::vector<std::vector<Unit>>> per(nb, std::vector<std::vector<Unit>>(g.n_det));
+        std::vector<double> cq(K), sq(K);
+        for (int q = 0; q < K; ++q) {
+            cq[q] = std::cos(kTwoPi * q / K);
+            sq[q] = std::sin(kTwoPi * q / K);
+        }
+        std::vector<double> rx0(ntx), rx1(ntx), ry0(nty), ry1(nty);
+        for (int tx = 0; tx < ntx; ++tx) {
+            rx0[tx] = ex[tx] - 1 - c0 - eps;
+            rx1[tx] = ex[tx + 1] - c0 + eps;
+        }
+        for (int ty = 0; ty < nty; ++ty) {
+            ry0[ty] = ey[ty] - 1 - c0 - eps;
+            ry1[ty] = ey[ty + 1] - c0 + eps;
+        }
+        std::vector<std::vector<std::vector<Unit>>> per(g.n_det, std::vector<std::vector<Unit>>(ntiles));
         const float* Uj = &detU[d.det_off];
         const float* Vj = &detV[d.det_off];
         parallel_for(g.n_det, [&](int j) {
-            std::vector<uint8_t> mark;
-            for (int b = 0; b < nb; ++b) {
-                const double x0 = -1.0 - c0 - eps, x1 = (double)(n - c0) + eps;
-                const double y0 = (double)(T.bands[b].lo - c0) - eps, y1 = (double)(T.bands[b].hi - c0) + eps;
-                for (int mb = 0; mb < d.nmb; ++mb) {
-                    const int m0 = mb * ml, m1 = std::min(m0 + ml, d.n_r) - 1;
-                    mark_chunks(Uj[j], Vj[j], m0 * (double)d.delta - eps, m1 * (double)d.delta + eps, x0, x1, y0, y1,
-                                K, G, mark);
-                    const int nch = (int)mark.size();
-                    std::vector<std::pair<int, int>> runs; // [c_begin, c_end), c_end > nch wraps
-                    int c = 0;
-                    while (c < nch) {
-                        if (!mark[c]) { ++c; continue; }
-                        int e = c;
-                        while (e < nch && mark[e]) ++e;
-                        runs.emplace_back(c, e);
-                        c = e;
+            std::vector<int> last(ntiles), start(ntiles);
+            std::vector<std::vector<std::pair<int, int>>> runs(ntiles);   // [q_begin, q_end)
+            for (int mb = 0; mb < d.nmb; ++mb) {
+                const int m0 = mb * ml, m1 = std::min(m0 + ml, d.n_r) - 1;
+                const double r0 = m0 * delta, r1 = m1 * delta;
+                std::fill(last.begin(), last.end(), -2);
+                for (auto& r : runs) r.clear();
+                for (int q = 0; q < K; ++q) {
+                    const double xa = Uj[j] + r0 * cq[q], xb = Uj[j] + r1 * cq[q];
+                    const double ya = Vj[j] + r0 * sq[q], yb = Vj[j] + r1 * sq[q];
+                    const double bx0 = std::min(xa, xb), bx1 = std::max(xa, xb);
+                    const double by0 = std::min(ya, yb), by1 = std::max(ya, yb);
+                    if (bx1 < rx0[0] || bx0 > rx1[ntx - 1] || by1 < ry0[0] || by0 > ry1[nty - 1]) continue;
+                    for (int ty = 0; ty < nty; ++ty) {
+                        if (by1 < ry0[ty] || by0 > ry1[ty]) continue;
+                        for (int tx = 0; tx < ntx; ++tx) {
+                            if (bx1 < rx0[tx] || bx0 > rx1[tx]) continue;
+                            const int t = ty * ntx + tx;
+                            if (last[t] != q - 1) {
+                                if (last[t] >= 0) runs[t].emplace_back(start[t], last[t] + 1);
+                                start[t] = q;
+                            }
+                            last[t] = q;
+                        }
                     }
-                    if (runs.size() >= 2 && runs.front().first == 0 && runs.back().second == nch) {
-                        runs.back().second = nch + runs.front().second;
-                        runs.erase(runs.begin());
+                }
+                for (int t = 0; t < ntiles; ++t) {
+                    if (last[t] >= 0) runs[t].emplace_back(start[t], last[t] + 1);
+                    auto& rr = runs[t];
+                    // a run through q = K - 1 continues at q = 0
+                    if (rr.size() >= 2 && rr.front().first == 0 && rr.back().second == K) {
+                        rr.back().second = K + rr.front().second;
+                        rr.erase(rr.begin());
                     }
-                    for (auto& r : runs) {
-                        int q0 = r.first * G;
-                        const int q1 = (r.second > nch) ? K + std::min((r.second - nch) * G, K)
-                                                        : std::min(r.second * G, K);
-                        int len = std::min(q1 - q0, K);
+                    for (auto& r : rr) {
+                        int q0 = r.first, len = r.second - r.first;
                         while (len > 0) {
                             // pieces never wrap past K (the kernel indexes K staged rays)
                             const int qs = q0 % K;
@@ -392,7 +430,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                             u.m0 = m0;
                             u.q0 = qs;
                             u.nq = piece;
-                            per[b][j].push_back(u);
+                            per[j][t].push_back(u);
                             q0 += piece;
                             len -= piece;
                         }
@@ -400,78 +438,105 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                 }
             }
         });
-        // slots per (detector, radius block), counted across bands in order
+        // slots per (detector, radius block), counted across tiles in order
         T.slotcnt.assign((size_t)g.n_det * d.nmb, 0);
-        for (int b = 0; b < nb; ++b)
+        for (int t = 0; t < ntiles; ++t)
             for (int j = 0; j < g.n_det; ++j)
-                for (Unit& u : per[b][j]) {
+                for (Unit& u : per[j][t]) {
                     int32_t& cnt = T.slotcnt[(size_t)j * d.nmb + u.m0 / ml];
                     u.slot = cnt++;
                     T.n_slots = std::max(T.n_slots, (int)cnt);
-                    T.slot_samples += (int64_t)u.nq * ml;
+                    T.slot_samples += (int64_t)((u.nq + QL - 1) / QL) * kWarp;
                 }
-        for (int b = 0; b < nb; ++b) {
-            auto& band = T.bands[b];
-            for (int j = 0; j < g.n_det; ++j)
-                band.units.insert(band.units.end(), per[b][j].begin(), per[b][j].end());
-            for (const Unit& u : band.units) band.cost += u.nq + kUnitOverhead;
+        for (int t = 0; t < ntiles; ++t) {
+            auto& tile = T.tiles[t];
+            for (int j = 0; j < g.n_det; ++j) tile.units.insert(tile.units.end(), per[j][t].begin(), per[j][t].end());
+            for (const Unit& u : tile.units) tile.cost += (double)(u.nq + QL - 1) / QL + kUnitOverhead;
         }
     }
 
     // ---- CTA schedule for the circular means ------------------------------
-    // Band tasks: (instance, band) with the band's units, largest first.  Each
-    // task gets CTAs in proportion to its cost (at least one); the CTAs of a
-    // task share its unit queue.  Participants are placed on CTAs by LPT.
-    const int smem_bytes = band_bytes + ray_bytes;
-    if (smem_bytes > P.max_smem_optin) return PAT_ERR_UNSUPPORTED;
+    // Tile tasks: (instance, tile).  Each task gets CTAs ("parts") in
+    // proportion to its cost (at least one); parts are placed on CTAs by LPT.
+    // Within a task, the units are spread over the parts' warps by LPT on
+    // their cost (a sample costs the same everywhere), once per template tile
+    // and part count, so identical instances share the schedule.
+    const int64_t smem_bytes64 = tile_bytes + ray_bytes;
+    if (smem_bytes64 > P.max_smem_optin) return PAT_ERR_UNSUPPORTED;
+    const int smem_bytes = (int)smem_bytes64;
     P.fwd_smem = smem_bytes;
     const int bps = circmean_blocks_per_sm(ml, bf16, smem_bytes);
     if (bps < 1) return PAT_ERR_UNSUPPORTED;
     const int n_ctas_target = bps * P.num_sms;
-    for (auto& T : tmpls)
-        for (auto& band : T.bands)
-            std::stable_sort(band.units.begin(), band.units.end(),
-                             [](const Unit& a, const Unit& b) { return a.nq > b.nq; });
-    std::vector<Unit> units;
-    for (auto& T : tmpls) {
-        T.band_unit_base.resize(T.bands.size());
-        for (size_t b = 0; b < T.bands.size(); ++b) {
-            T.band_unit_base[b] = (int64_t)units.size();
-            units.insert(units.end(), T.bands[b].units.begin(), T.bands[b].units.end());
+    constexpr int kWarpsCta = kCircThreads / kWarp;
+    auto unit_cost = [&](const Unit& u) { return (double)((u.nq + QL - 1) / QL) + kUnitOverhead; };
+    double total_cost = 0.0;
+    for (int i = 0; i < n_inst; ++i)
+        for (const auto& tt : tmpls[inst_tmpl[i]].tiles) total_cost += tt.cost;
+    // parts per template tile
+    std::vector<std::vector<int>> tile_parts(tmpls.size());
+    for (size_t t = 0; t < tmpls.size(); ++t) {
+        tile_parts[t].resize(tmpls[t].tiles.size(), 0);
+        for (size_t k = 0; k < tmpls[t].tiles.size(); ++k) {
+            const TileTemplate& tt = tmpls[t].tiles[k];
+            if (tt.units.empty()) continue;
+            const double share = tt.cost / std::max(total_cost, 1.0) * n_ctas_target;
+            const int nunits = (int)tt.units.size();
+            tile_parts[t][k] = std::max(1, std::min((int)std::lround(share), std::max(1, nunits / (2 * kWarpsCta))));
         }
     }
-    struct TaskC {
-        Segment s;
-        double cost;
-    };
-    std::vector<TaskC> tasks;
-    double total_cost = 0.0;
-    for (int i = 0; i < n_inst; ++i) {
-        const GeomTemplate& T = tmpls[inst_tmpl[i]];
-        for (size_t b = 0; b < T.bands.size(); ++b) {
-            if (T.bands[b].units.empty()) continue;
-            Segment s{};
-            s.inst = i;
-            s.band_lo = T.bands[b].lo;
-            s.band_hi = T.bands[b].hi;
-            s.unit_begin = (int32_t)T.band_unit_base[b];
-            s.unit_end = (int32_t)(T.band_unit_base[b] + T.bands[b].units.size());
-            s.queue = (int32_t)tasks.size();
-            tasks.push_back({s, T.bands[b].cost});
-            total_cost += T.bands[b].cost;
+    // per (template tile): units grouped by (part, warp); offsets per warp
+    std::vector<Unit> units;
+    std::vector<int32_t> warp_units;
+    std::vector<std::vector<int32_t>> tile_woff(tmpls.size());   // first warp_units index of (tile, part 0)
+    for (size_t t = 0; t < tmpls.size(); ++t) {
+        tile_woff[t].assign(tmpls[t].tiles.size(), -1);
+        for (size_t k = 0; k < tmpls[t].tiles.size(); ++k) {
+            const TileTemplate& tt = tmpls[t].tiles[k];
+            const int np = tile_parts[t][k];
+            if (np == 0) continue;
+            const int nw = np * kWarpsCta;
+            std::vector<std::vector<Unit>> lists(nw);
+            using E = std::pair<double, int>;
+            std::priority_queue<E, std::vector<E>, std::greater<E>> pq;
+            for (int w = 0; w < nw; ++w) pq.push({0.0, w});
+            for (const Unit& u : tt.units) {   // units are sorted largest first
+                E e = pq.top();
+                pq.pop();
+                lists[e.second].push_back(u);
+                pq.push({e.first + unit_cost(u), e.second});
+            }
+            tile_woff[t][k] = (int32_t)warp_units.size();
+            for (int w = 0; w < nw; ++w) {
+                warp_units.push_back((int32_t)units.size());
+                units.insert(units.end(), lists[w].begin(), lists[w].end());
+            }
+            warp_units.push_back((int32_t)units.size());   // end of the last warp (one slot per tile)
         }
     }
     struct PartC {
-        int task;
+        Segment s;
         double cost;
     };
     std::vector<PartC> parts;
-    for (size_t t = 0; t < tasks.size(); ++t) {
-        const double share = tasks[t].cost / std::max(total_cost, 1.0) * n_ctas_target;
-        const int nunits = tasks[t].s.unit_end - tasks[t].s.unit_begin;
-        const int np = std::max(1, std::min((int)std::lround(share), std::max(1, nunits / 2)));
-        tasks[t].s.parts = np;
-        for (int k = 0; k < np; ++k) parts.push_back({(int)t, tasks[t].cost / np});
+    for (int i = 0; i < n_inst; ++i) {
+        const int t = inst_tmpl[i];
+        const GeomTemplate& T = tmpls[t];
+        for (size_t k = 0; k < T.tiles.size(); ++k) {
+            const TileTemplate& tt = T.tiles[k];
+            const int np = tile_parts[t][k];
+            for (int p = 0; p < np; ++p) {
+                Segment s{};
+                s.inst = i;
+                s.x0 = tt.x0;
+                s.x1 = tt.x1;
+                s.y0 = tt.y0;
+                s.y1 = tt.y1;
+                s.pitch = cell_pitch(tt.x1 - tt.x0);
+                s.warp_off = tile_woff[t][k] + p * kWarpsCta;
+                parts.push_back({s, tt.cost / np});
+            }
+        }
     }
     std::stable_sort(parts.begin(), parts.end(), [](const PartC& a, const PartC& b) { return a.cost > b.cost; });
     const int n_ctas = std::max(1, std::min(n_ctas_target, (int)parts.size()));
@@ -483,7 +548,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (const PartC& p : parts) {
             E e = pq.top();
             pq.pop();
-            cta_lists[e.second].push_back(tasks[p.task].s);
+            cta_lists[e.second].push_back(p.s);
             pq.push({e.first + p.cost + 8.0 * kUnitOverhead, e.second});
         }
     }
@@ -494,7 +559,9 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         cta_seg.push_back((int32_t)segs.size());
     }
     if (parts.empty()) cta_seg.assign(1, 0);
-    const int64_t n_band_tasks = (int64_t)tasks.size();
+    std::vector<int2> msum_rows;
+    for (int i = 0; i < n_inst; ++i)
+        for (int j = 0; j < geoms[i].n_det; ++j) msum_rows.push_back(make_int2(i, j));
 
     // ---- adjoint cell items -------------------------------------------------
     int64_t patches = 0;
@@ -506,9 +573,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     if (cbps < 1) return PAT_ERR_UNSUPPORTED;
     const int64_t resident_warps = (int64_t)cbps * P.num_sms * 8;
     // adjoint list mode is chosen here (the sample count used for the budget is
-    // the forward's evaluated-sample upper bound); its groups split each list.
-    // Instances with the same geometry share one template's lists, so each
-    // template counts once.
+    // the forward's evaluated-sample upper bound).  Instances with the same
+    // geometry share one template's lists, so each template counts once.
     int64_t slot_samples_all = 0;
     {
         std::vector<char> seen(tmpls.size(), 0);
@@ -556,15 +622,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             }
     }
     std::stable_sort(wit.begin(), wit.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    int LG = 1;
-    if (use_lists) {
-        const int lbps = adj_list_blocks_per_sm(frac_lists);
-        if (lbps < 1) return PAT_ERR_UNSUPPORTED;
-        const int64_t lres = (int64_t)lbps * P.num_sms * 8;
-        LG = opt.adj_groups > 0 ? opt.adj_groups
-                                : (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * lres + patches - 1) / patches));
-    }
-    const int ZG = use_lists ? LG : AG;
+    const int ZG = use_lists ? 1 : AG;   // list mode writes one corner-sum plane
     std::vector<CellItem> citems;
     citems.reserve(wit.size());
     for (auto& w : wit) citems.push_back(w.second);
@@ -574,7 +632,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     // ---- per-instance workspace offsets and slot counts -------------------
     std::vector<int32_t> slotcnt;
     std::map<int, int64_t> tmpl_slot_off;
-    int64_t mpart_total = 0, mbar_total = 0, z_total = 0, arrive_total = 0;
+    int64_t mpart_total = 0, mbar_total = 0, z_total = 0;
     int64_t samples_slots = 0;
     for (int i = 0; i < n_inst; ++i) {
         const int ti = inst_tmpl[i];
@@ -589,9 +647,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         d.mpart_off = mpart_total;
         mpart_total += (int64_t)T.n_slots * d.n_det * d.n_r;
         d.mbar_off = mbar_total;
-        mbar_total += (int64_t)d.n_det * d.n_rp;
-        d.arrive_off = arrive_total;
-        arrive_total += (int64_t)d.n_det * d.nmb;
+        mbar_total += (int64_t)d.n_det * d.m_pitch;
         d.z_off = z_total;
         z_total += (int64_t)ZG * (d.n + 1) * (d.n + 1);
         samples_slots += T.slot_samples;
@@ -643,6 +699,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const size_t o_P = reserve(sizeof(float) * pmat.size());
     const size_t o_slot = reserve(sizeof(int32_t) * slotcnt.size());
     const size_t o_units = reserve(sizeof(Unit) * units.size());
+    const size_t o_wunits = reserve(sizeof(int32_t) * warp_units.size());
+    const size_t o_msrows = reserve(sizeof(int2) * msum_rows.size());
     const size_t o_segs = reserve(sizeof(Segment) * segs.size());
     const size_t o_ctaseg = reserve(sizeof(int32_t) * cta_seg.size());
     const size_t o_ft = reserve(sizeof(TimeTile) * fwd_tiles.size());
@@ -668,6 +726,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     put(o_P, pmat.data(), sizeof(float) * pmat.size());
     put(o_slot, slotcnt.data(), sizeof(int32_t) * slotcnt.size());
     put(o_units, units.data(), sizeof(Unit) * units.size());
+    put(o_wunits, warp_units.data(), sizeof(int32_t) * warp_units.size());
+    put(o_msrows, msum_rows.data(), sizeof(int2) * msum_rows.size());
     put(o_segs, segs.data(), sizeof(Segment) * segs.size());
     put(o_ctaseg, cta_seg.data(), sizeof(int32_t) * cta_seg.size());
     put(o_ft, fwd_tiles.data(), sizeof(TimeTile) * fwd_tiles.size());
@@ -681,9 +741,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     // workspace (4-byte words): slots | M | Mbar | TV partials | arrival counters | cell sums (float4)
     const int64_t tv_parts = 3 * (int64_t)itiles.size();
     const int64_t o_msum = mpart_total, o_mbar = o_msum + mbar_total, o_tvp = o_mbar + mbar_total;
-    const int64_t o_arr = o_tvp + tv_parts;
-    const int64_t o_ctr = ((o_arr + arrive_total + kQueueStride - 1) / kQueueStride) * kQueueStride;
-    const int64_t n_ctr = (2 + (int64_t)n_band_tasks) * kQueueStride;
+    const int64_t o_ctr = ((o_tvp + tv_parts + kQueueStride - 1) / kQueueStride) * kQueueStride;
+    const int64_t n_ctr = 2 * (int64_t)kQueueStride;
     const int64_t o_res = ((o_ctr + n_ctr + 63) / 64) * 64;   // data residual of pat_tv_step
     const int64_t z_float_off = ((o_res + P.g_offsets[n_inst] + 63) / 64) * 64;
     P.work_floats = z_float_off + 4 * z_total;
@@ -692,8 +751,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         cudaGetLastError();
         return PAT_ERR_OOM;
     }
-    // zero everything once: circular-mean sums of blocks that no unit touches
-    // stay zero, and the arrival counters start (and are left by every call) at 0
+    // zero everything once: the work-queue counters start (and are left by
+    // every call) at 0, and the columns of M and Mbar from n_r on stay zero
     if (cudaMemsetAsync(P.d_work, 0, sizeof(float) * std::max<int64_t>(P.work_floats, 1), st) != cudaSuccess)
         return PAT_ERR_CUDA;
 
@@ -707,6 +766,11 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.P = reinterpret_cast<const float*>(base + o_P);
     dp.slotcnt = reinterpret_cast<const uint8_t*>(base + o_slot);
     dp.units = reinterpret_cast<const Unit*>(base + o_units);
+    dp.warp_units = reinterpret_cast<const int32_t*>(base + o_wunits);
+    dp.msum_rows = reinterpret_cast<const int2*>(base + o_msrows);
+    dp.n_msum_rows = (int32_t)msum_rows.size();
+    dp.n_r_max = 0;
+    for (int i = 0; i < n_inst; ++i) dp.n_r_max = std::max(dp.n_r_max, inst[i].n_r);
     dp.segs = reinterpret_cast<const Segment*>(base + o_segs);
     dp.cta_seg = reinterpret_cast<const int32_t*>(base + o_ctaseg);
     dp.fwd_tiles = reinterpret_cast<const TimeTile*>(base + o_ft);
@@ -717,11 +781,10 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.msum = P.d_work + o_msum;
     dp.mbar = P.d_work + o_mbar;
     dp.tv_partial = P.d_work + o_tvp;
-    dp.slot_arrivals = reinterpret_cast<int32_t*>(P.d_work + o_arr);
     dp.work_counters = reinterpret_cast<int32_t*>(P.d_work + o_ctr);
     P.d_resid = P.d_work + o_res;
-    P.d_counters = reinterpret_cast<int32_t*>(P.d_work + o_arr);
-    P.counters_bytes = (size_t)(o_ctr + n_ctr - o_arr) * 4;
+    P.d_counters = reinterpret_cast<int32_t*>(P.d_work + o_ctr);
+    P.counters_bytes = (size_t)n_ctr * 4;
     dp.zbuf = reinterpret_cast<float4*>(P.d_work + z_float_off);
     dp.status = reinterpret_cast<int32_t*>(base + o_status);
     dp.n_inst = n_inst;
@@ -734,7 +797,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.adj_groups = AG;
     dp.cell_blocks = cell_blocks;
     dp.fwd_smem_bytes = smem_bytes;
-    dp.fwd_rays_off = band_bytes;
+    dp.fwd_rays_off = (int32_t)tile_bytes;
     dp.abel_cluster_fwd = cluster_for(fwd_tiles.size());
     dp.abel_cluster_adj = cluster_for(adj_tiles.size());
     dp.bf16 = bf16 ? 1 : 0;
@@ -763,14 +826,10 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     }
 
     // ---- adjoint sample lists (list mode) --------------------------------------
-    // Hits are counted per cell, then stored per (8 x 4 patch, part): the 32
-    // cells' parts interleaved vector by vector, each block as long as the
-    // patch's longest part (see k_adj_build).
+    // Hits are counted per cell, then stored per cell, contiguous, padded
+    // to kListPad entries (see pat_internal.h and k_adj_build).
     int64_t list_bytes = 0;
     if (use_lists) {
-        const int S = frac_lists ? 3 : 1;     // 16-byte slots per vector of four samples
-        const int G = LG;
-        dp.adj_groups = G;                    // the fill kernel splits lists into G parts
         // count the hits of every cell, per geometry template (first instance)
         std::vector<int> rep(tmpls.size(), -1);
         for (int i = 0; i < n_inst; ++i)
@@ -788,7 +847,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
             const int i = rep[t];
             const int cells = (inst[i].n + 1) * (inst[i].n + 1);
-            if (launch_adj_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, false, st) != cudaSuccess)
+            if (launch_adj_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, nullptr, nullptr, st) != cudaSuccess)
                 s = PAT_ERR_CUDA;
             counts[t].resize(cells);
             if (s == PAT_OK && cudaMemcpyAsync(counts[t].data(), d_counts, sizeof(int32_t) * cells,
@@ -798,58 +857,43 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         }
         cudaFree(d_counts);
         if (s != PAT_OK) return s;
-        // block bases per (template, patch, part) and the longest part of each
-        std::vector<int32_t> cnt_all;
-        std::vector<int64_t> pbase_all;
-        std::vector<int64_t> tmpl_cnt_off(tmpls.size()), tmpl_pbase_off(tmpls.size());
-        std::vector<std::vector<int32_t>> part_len(tmpls.size());
-        int64_t slots_total = 0;   // 16-byte slots
+        // cell starts per template (padded lengths), one extra entry each
+        std::vector<int64_t> start_all;
+        std::vector<int64_t> tmpl_start_off(tmpls.size());
+        std::vector<std::vector<int32_t>> padded(tmpls.size());
+        int64_t entries = 0;
         for (size_t t = 0; t < tmpls.size(); ++t) {
-            const int n = inst[rep[t]].n, w = n + 1;
-            const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
-            tmpl_cnt_off[t] = (int64_t)cnt_all.size();
-            cnt_all.insert(cnt_all.end(), counts[t].begin(), counts[t].end());
-            tmpl_pbase_off[t] = (int64_t)pbase_all.size();
-            part_len[t].assign((size_t)pw * ph * G, 0);
-            for (int py = 0; py < ph; ++py)
-                for (int px = 0; px < pw; ++px)
-                    for (int g = 0; g < G; ++g) {
-                        int V = 0;
-                        for (int dy = 0; dy < kPatchH; ++dy)
-                            for (int dx = 0; dx < kPatchW; ++dx) {
-                                const int cxa = px * kPatchW + dx, cya = py * kPatchH + dy;  // cell + 1
-                                if (cxa >= w || cya >= w) continue;
-                                const int nv = (counts[t][(size_t)cya * w + cxa] + 3) >> 2;
-                                const int v0 = (int)(((int64_t)g * nv) / G), v1 = (int)(((int64_t)(g + 1) * nv) / G);
-                                V = std::max(V, v1 - v0);
-                            }
-                        part_len[t][((size_t)py * pw + px) * G + g] = V;
-                        pbase_all.push_back(slots_total);
-                        slots_total += (int64_t)V * S * kWarp;
-                    }
-            for (int i = 0; i < n_inst; ++i)
-                if (inst_tmpl[i] == (int)t) inst[i].patches_x = pw;
+            tmpl_start_off[t] = (int64_t)start_all.size();
+            padded[t].resize(counts[t].size());
+            for (size_t c = 0; c < counts[t].size(); ++c) {
+                padded[t][c] = (counts[t][c] + kListPad - 1) / kListPad * kListPad;
+                start_all.push_back(entries);
+                entries += padded[t][c];
+            }
+            start_all.push_back(entries);
         }
-        // list-mode work items: (patch, part), longest part first
+        // work items: 2 x 2 cell blocks, longest list first
         std::vector<std::pair<int32_t, CellItem>> li;
         for (int i = 0; i < n_inst; ++i) {
             const int t = inst_tmpl[i];
             const int n = inst[i].n, w = n + 1;
-            const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
-            for (int py = 0; py < ph; ++py)
-                for (int px = 0; px < pw; ++px)
-                    for (int g = 0; g < G; ++g) {
-                        const int32_t V = part_len[t][((size_t)py * pw + px) * G + g];
-                        if (V > 0) li.push_back({V, CellItem{i, px * kPatchW - 1, py * kPatchH - 1, g}});
-                    }
+            for (int y0 = -1; y0 <= n - 1; y0 += 2)
+                for (int x0 = -1; x0 <= n - 1; x0 += 2) {
+                    int32_t L = 0;
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx)
+                            if (x0 + dx <= n - 1 && y0 + dy <= n - 1)
+                                L = std::max(L, padded[t][(size_t)(y0 + dy + 1) * w + (x0 + dx + 1)]);
+                    if (L > 0) li.push_back({L, CellItem{i, x0, y0, 0}});
+                }
         }
         std::stable_sort(li.begin(), li.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-        const size_t b_pbase = sizeof(int64_t) * std::max<size_t>(pbase_all.size(), 1);
-        const size_t b_cnt = sizeof(int32_t) * cnt_all.size();
+        const size_t b_start = sizeof(int64_t) * start_all.size();
         const size_t b_items = sizeof(CellItem) * std::max<size_t>(li.size(), 1);
-        const size_t b_codes = 16 * (size_t)std::max<int64_t>(slots_total, 1);
-        const size_t o_cnt_l = align(b_pbase), o_items_l = align(o_cnt_l + b_cnt), o_codes_l = align(o_items_l + b_items);
-        list_bytes = (int64_t)(o_codes_l + b_codes);
+        const size_t b_codes = 4 * (size_t)std::max<int64_t>(entries, 1);
+        const size_t o_items_l = align(b_start), o_codes_l = align(o_items_l + b_items);
+        const size_t o_fa = align(o_codes_l + b_codes), o_fb = align(o_fa + (frac_lists ? b_codes : 0));
+        list_bytes = (int64_t)(frac_lists ? o_fb + b_codes : o_fa);
         if (cudaMalloc(&P.d_lists, list_bytes) != cudaSuccess) {
             P.d_lists = nullptr;
             cudaGetLastError();
@@ -858,39 +902,36 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         unsigned char* lb = static_cast<unsigned char*>(P.d_lists);
         std::vector<CellItem> items(li.size());
         for (size_t k = 0; k < li.size(); ++k) items[k] = li[k].second;
-        if (cudaMemcpyAsync(lb, pbase_all.data(), sizeof(int64_t) * pbase_all.size(), cudaMemcpyHostToDevice, st) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(lb + o_cnt_l, cnt_all.data(), b_cnt, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        if (cudaMemcpyAsync(lb, start_all.data(), b_start, cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemcpyAsync(lb + o_items_l, items.data(), sizeof(CellItem) * items.size(), cudaMemcpyHostToDevice,
-                            st) != cudaSuccess ||
-            cudaMemsetAsync(lb + o_codes_l, 0, b_codes, st) != cudaSuccess)
+                            st) != cudaSuccess)
             return PAT_ERR_CUDA;
-        dp.list_base = reinterpret_cast<const int64_t*>(lb);
-        dp.cell_cnt = reinterpret_cast<const int32_t*>(lb + o_cnt_l);
+        dp.cell_start = reinterpret_cast<const int64_t*>(lb);
         dp.list_items = reinterpret_cast<const CellItem*>(lb + o_items_l);
         dp.codes = reinterpret_cast<const uint32_t*>(lb + o_codes_l);
-        for (int i = 0; i < n_inst; ++i) {
-            inst[i].list_off = tmpl_cnt_off[inst_tmpl[i]];
-            inst[i].pbase_off = tmpl_pbase_off[inst_tmpl[i]];
-        }
+        dp.frac_a = frac_lists ? reinterpret_cast<const float*>(lb + o_fa) : nullptr;
+        dp.frac_b = frac_lists ? reinterpret_cast<const float*>(lb + o_fb) : nullptr;
+        for (int i = 0; i < n_inst; ++i) inst[i].list_off = tmpl_start_off[inst_tmpl[i]];
         if (cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(InstDev) * inst.size(), cudaMemcpyHostToDevice, st) !=
             cudaSuccess)
             return PAT_ERR_CUDA;
-        // fill the lists (same enumeration, same order)
+        // fill the lists (same enumeration, same order), padding included
         for (size_t t = 0; t < tmpls.size(); ++t) {
             const int i = rep[t];
-            if (launch_adj_build(dp, i, inst[i].n, const_cast<int32_t*>(dp.cell_cnt) + tmpl_cnt_off[t],
-                                 dp.list_base + tmpl_pbase_off[t], reinterpret_cast<uint32_t*>(lb + o_codes_l),
-                                 frac_lists, st) != cudaSuccess)
+            if (launch_adj_build(dp, i, inst[i].n, nullptr, dp.cell_start + tmpl_start_off[t],
+                                 reinterpret_cast<uint32_t*>(lb + o_codes_l),
+                                 frac_lists ? reinterpret_cast<float*>(lb + o_fa) : nullptr,
+                                 frac_lists ? reinterpret_cast<float*>(lb + o_fb) : nullptr, st) != cudaSuccess)
                 return PAT_ERR_CUDA;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
         dp.n_list_items = (int)li.size();
         dp.adj_mode = frac_lists ? 3 : 1;
         const int lbps = adj_list_blocks_per_sm(frac_lists);
+        if (lbps < 1) return PAT_ERR_UNSUPPORTED;
         dp.cell_blocks = (int)std::max<int64_t>(
             1, std::min<int64_t>((int64_t)lbps * P.num_sms, ((int64_t)li.size() + 7) / 8));
-        dp.adj_groups = LG;
+        dp.adj_groups = 1;
     }
 
     // ---- info -------------------------------------------------------------
@@ -908,15 +949,19 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     I.m_lanes = ml;
     I.q_piece = qpiece;
     I.band_rows = 0;
+    I.tile_cols = 0;
     for (auto& T : tmpls)
-        for (auto& b : T.bands) I.band_rows = std::max(I.band_rows, b.hi - b.lo + 1);
+        for (auto& t : T.tiles) {
+            I.band_rows = std::max(I.band_rows, t.y1 - t.y0);
+            I.tile_cols = std::max(I.tile_cols, t.x1 - t.x0);
+        }
     I.adj_groups = dp.adj_groups;
     I.adj_mode = dp.adj_mode == 0 ? 2 : dp.adj_mode;
     I.abel_split_fwd = dp.abel_cluster_fwd;
     I.abel_split_adj = dp.abel_cluster_adj;
     I.list_bytes = list_bytes;
     I.device_bytes += list_bytes;
-    I.bands_max = bands_max;
+    I.bands_max = tiles_max;
     return PAT_OK;
 }
 

@@ -18,7 +18,7 @@ struct Plan {
     int device = 0;
     int num_sms = 0;
     int n_inst = 0;
-    int band_budget_bytes = 100 * 1024;  // default shared band size (2 CTAs per SM)
+    int band_budget_bytes = 110 * 1024;  // default shared memory of a circular-mean CTA (2 per SM)
     int max_smem_optin = 227 * 1024;
     pat_options_t opt{};
     std::vector<pat_geometry_t> geoms;

@@ -1,7 +1,7 @@
 // tune.cpp — autotuner for the tile shapes of a plan.
 //
 // Candidates for the circular-mean kernel (radii per warp, angles per unit,
-// rows per shared-memory band) are timed on the plan's own geometries with
+// tile width) are timed on the plan's own geometries with
 // CUDA events, then the cluster split of the two time stages, then candidates
 // for the adjoint gather (list format, list parts) with the best shapes so
 // far; the fastest plan is kept.  Results are cached per
@@ -27,11 +27,24 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::string, pat_options_t> g_tune_cache;
 
+// Cache key from the geometries' fields (not their struct bytes, whose
+// padding a C caller may leave uninitialised), the image dtype and the device.
 std::string tune_key(const pat_geometry_t* geoms, int n, const pat_options_t& opt, int device)
 {
-    std::string k(reinterpret_cast<const char*>(geoms), sizeof(pat_geometry_t) * (size_t)n);
-    k.append(reinterpret_cast<const char*>(&opt.image_dtype), sizeof(int32_t));
-    k.append(reinterpret_cast<const char*>(&device), sizeof(int));
+    std::string k;
+    auto put = [&k](const void* p, size_t b) { k.append(static_cast<const char*>(p), b); };
+    for (int i = 0; i < n; ++i) {
+        const pat_geometry_t& g = geoms[i];
+        put(&g.n, sizeof g.n);
+        put(&g.n_det, sizeof g.n_det);
+        put(&g.arc_start, sizeof g.arc_start);
+        put(&g.arc_span, sizeof g.arc_span);
+        put(&g.n_t, sizeof g.n_t);
+        put(&g.t_max, sizeof g.t_max);
+        put(&g.n_angles, sizeof g.n_angles);
+    }
+    put(&opt.image_dtype, sizeof opt.image_dtype);
+    put(&device, sizeof device);
     return k;
 }
 
@@ -127,33 +140,24 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
     cudaMemsetAsync(d_g, 0, (size_t)g_elems * 4, st);
 
     // ---- forward candidates ---------------------------------------------
-    const int W = bf16 ? band_pitch_bf16(n_max) : band_pitch_f32(n_max);
-    const int esize = bf16 ? 2 : 4;
-    int K_max = 0;
-    for (int i = 0; i < n_inst; ++i) K_max = std::max(K_max, geoms[i].n_angles);
-    const int max_rows = (227 * 1024 - K_max * 16) / (W * esize);
-    std::vector<int> rows_cands = {0};
-    for (int nb : {1, 2, 4, 6}) {
-        const int rows = (n_max + 1 + nb - 1) / nb + 1;
-        if (rows <= max_rows && rows >= 3) rows_cands.push_back(rows);
-    }
-    // large images: a few fixed band heights (the default budget gives short
-    // bands there, and units then cross many band edges)
-    for (int rows : {32, 48})
-        if (rows <= max_rows && 6 * (rows - 1) < n_max + 1) rows_cands.push_back(rows);
+    // tile widths: automatic (fewest tile edges), full width, half, quarter
+    const bool large = f_elems > (1 << 20);   // keep the search short on big plans
+    std::vector<int> cols_cands = {0};
+    for (int div : large ? std::vector<int>{2} : std::vector<int>{1, 2, 4})
+        if (n_max / div >= 32) cols_cands.push_back((n_max + div - 1) / div);
     Plan* best = nullptr;
     float best_ms = 1e30f;
     pat_options_t best_opt = opt;
-    const bool large = f_elems > (1 << 20);   // keep the search short on big plans
-    const std::vector<int> ml_c = large ? std::vector<int>{32} : std::vector<int>{32, 16};
-    const std::vector<int> qp_c = large ? std::vector<int>{128, 256} : std::vector<int>{64, 128, 256};
+    const std::vector<int> ml_c = large ? std::vector<int>{16, 8} : std::vector<int>{32, 16, 8};
+    const std::vector<int> qp_c = large ? std::vector<int>{256} : std::vector<int>{64, 128, 256};
     for (int ml : ml_c) {
         for (int qp : qp_c) {
-            for (int rows : rows_cands) {
+            for (int cols : cols_cands) {
                 pat_options_t o = opt;
                 o.m_lanes = ml;
                 o.q_piece = qp;
-                o.band_rows = rows;
+                o.tile_cols = cols;
+                o.band_rows = 0;
                 o.adj_mode = 2;      // the adjoint is tuned below; skip list building here
                 o.adj_groups = 1;
                 Plan* p = try_build(geoms, n_inst, o, st);
@@ -194,9 +198,12 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
     // ---- adjoint candidates (with the best forward shape) ------------------
     best_ms = 1e30f;
     pat_options_t fwd_opt = best_opt;
+    // list modes have no further shape; the enumeration mode splits detectors into groups
     std::vector<std::pair<int, int>> adj_cands;
-    for (int mode : opt.adj_mode == 0 ? std::vector<int>{0, 1} : std::vector<int>{opt.adj_mode})
-        for (int gcount : {0, 1, 2, 4, 8}) adj_cands.push_back({mode, gcount});
+    if (opt.adj_mode == 2)
+        for (int gcount : {0, 1, 2, 4, 8}) adj_cands.push_back({2, gcount});
+    else
+        adj_cands.push_back({opt.adj_mode, 0});
     for (auto& ac : adj_cands) {
         pat_options_t o = fwd_opt;
         o.adj_mode = ac.first;

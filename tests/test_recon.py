@@ -28,7 +28,16 @@ def test_unet_shapes_and_nonnegativity():
     assert net.enc[3][0].out_channels == 64 and net.dec[2][0].out_channels == 8
     m = UNet(in_ch=4, base=8, mouse=True)
     assert m.head.bias is None and m.head.kernel_size == (1, 1)
-    assert float(m(x).min()) < 0.0 or True  # LeakyReLU output may be negative
+    # LeakyReLU(0.125) output: flipping the sign of the 1x1 head flips the sign
+    # of every pre-activation, so the two outputs are y+ and -0.125 y+ apart
+    with torch.no_grad():
+        ya = m(x)
+        m.head.weight.neg_()
+        yb = m(x)
+    pre = torch.where(ya >= 0, ya, ya / 0.125)        # undo the activation
+    expect = torch.where(-pre >= 0, -pre, -0.125 * pre)
+    assert torch.allclose(yb, expect, rtol=1e-5, atol=1e-6)
+    assert float(torch.minimum(ya, yb).min()) < 0.0     # negative outputs occur
 
 
 def test_unet_paper_channel_plan():
