@@ -111,7 +111,10 @@ typedef struct {
     int32_t abel_split;  /* CTAs (a thread-block cluster) sharing each time-stage tile: 1, 2, */
                          /*   4 or 8; 0 = auto (more when there are fewer tiles than SMs)     */
     int32_t tile_cols;   /* max pixel columns of a circular-mean tile; 0 = auto               */
-    int32_t reserved[6];
+    int32_t time_pair;   /* time stages of pat_tv_step / pat_pdhg_step: 0 = auto (one fused   */
+                         /*   launch per step where its shared memory fits: n_t up to ~2400), */
+                         /*   1 = separate launches (radius sums, forward, adjoint)          */
+    int32_t reserved[5];
 } pat_options_t;
 
 /* Plan statistics (pat_plan_info). */
@@ -133,7 +136,7 @@ typedef struct {
     int32_t abel_split_fwd;  /* CTAs per forward / adjoint time-stage tile in use         */
     int32_t abel_split_adj;
     int32_t tile_cols;       /* widest circular-mean tile (pixels); band_rows the tallest */
-    int32_t reserved[1];
+    int32_t time_pair;       /* 1 = the steps run the fused time stage, 0 = separate      */
 } pat_plan_info_t;
 
 /*
@@ -224,10 +227,14 @@ pat_status_t pat_descent_step(pat_plan_t plan, float* d_f, const float* d_adj,
  * pat_tv_step — one projected-gradient iteration of the TV reconstruction of
  * Eq. (4), min_{f >= 0} 1/2 ||A f - g||^2 + lam TV_eps(f):
  *     r = A f_in - g;   f_out = max(0, f_in - tau (A^T r + lam grad TV_eps(f_in)))
- * (the max only when nonneg != 0).  Same result as pat_forward, pat_residual,
- * pat_adjoint, pat_tv_grad and pat_descent_step in sequence, in fewer kernels:
- * the residual is formed in the time stage of A, and the adjoint's final pixel
- * sums, the TV gradient and the update share one kernel.  FP32 plans.
+ * (the max only when nonneg != 0).  Same arithmetic as pat_forward,
+ * pat_residual, pat_adjoint, pat_tv_grad and pat_descent_step in sequence, in
+ * fewer kernels: the adjoint's final pixel sums, the TV gradient and the
+ * update share one kernel, and the time stages of A and A^T with the residual
+ * between them are one launch (pat_options_t.time_pair = 0, where it fits;
+ * it adds the contractions of the time stages in another order, so the result
+ * matches the separate calls to FP32 rounding; with time_pair = 1 it is the
+ * same bit for bit).  FP32 plans.
  *   d_f_in:  device FP32 images (read only).   d_f_out: device FP32 images,
  *            overwritten; must not alias d_f_in (the TV stencil reads the old
  *            neighbours).   d_g: device FP32 measured data (read only).
@@ -310,12 +317,13 @@ pat_status_t pat_plan_set_wait_probe(pat_plan_t plan, int32_t clocks);
  * (host arrays of n_kinds entries, either may be NULL) and forgets them.
  * Kinds (pat_kernel_kind_t order): circular means, Abel forward, Abel
  * adjoint, adjoint gather, TV, residual, descent step, fused TV update,
- * primal-dual TV dual step, primal-dual primal step.
+ * primal-dual TV dual step, primal-dual primal step, fused time stage of
+ * the steps (radius sums + Abel forward + residual + Abel adjoint).
  */
 typedef enum {
     PAT_K_CIRCMEAN = 0, PAT_K_ABEL_FWD = 1, PAT_K_ABEL_ADJ = 2, PAT_K_ADJ_GATHER = 3,
     PAT_K_TV = 4, PAT_K_RESIDUAL = 5, PAT_K_DESCENT = 6, PAT_K_TV_UPDATE = 7, PAT_K_PDHG_DUAL = 8,
-    PAT_K_PDHG_PRIMAL = 9, PAT_K_COUNT = 10
+    PAT_K_PDHG_PRIMAL = 9, PAT_K_TIME_PAIR = 10, PAT_K_COUNT = 11
 } pat_kernel_kind_t;
 pat_status_t pat_plan_set_timing(pat_plan_t plan, int32_t enable);
 pat_status_t pat_plan_kernel_times(pat_plan_t plan, double* total_ms, int64_t* launches, int32_t n_kinds);

@@ -26,7 +26,7 @@ EXPORTED = (
     "pat_plan_set_wait_probe", "pat_status_string",
 )
 KERNEL_KINDS = ("circmean", "abel_fwd", "abel_adj", "adjoint_gather", "tv", "residual", "descent", "tv_update",
-                "pdhg_dual", "pdhg_primal")
+                "pdhg_dual", "pdhg_primal", "time_pair")
 
 
 class PatGeometry(ctypes.Structure):
@@ -42,7 +42,7 @@ class PatOptions(ctypes.Structure):
         ("image_dtype", ctypes.c_int32), ("schedule", ctypes.c_int32), ("tune", ctypes.c_int32),
         ("m_lanes", ctypes.c_int32), ("q_piece", ctypes.c_int32), ("band_rows", ctypes.c_int32),
         ("adj_groups", ctypes.c_int32), ("adj_mode", ctypes.c_int32), ("abel_split", ctypes.c_int32),
-        ("tile_cols", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
+        ("tile_cols", ctypes.c_int32), ("time_pair", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -54,7 +54,7 @@ class PatPlanInfo(ctypes.Structure):
         ("m_lanes", ctypes.c_int32), ("q_piece", ctypes.c_int32), ("band_rows", ctypes.c_int32),
         ("adj_groups", ctypes.c_int32), ("bands_max", ctypes.c_int32), ("adj_mode", ctypes.c_int32),
         ("list_bytes", ctypes.c_int64), ("abel_split_fwd", ctypes.c_int32), ("abel_split_adj", ctypes.c_int32),
-        ("tile_cols", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+        ("tile_cols", ctypes.c_int32), ("time_pair", ctypes.c_int32),
     ]
 
 

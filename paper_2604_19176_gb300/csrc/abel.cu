@@ -212,4 +212,349 @@ cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st)
     return launch_abel<false>(dp, dp.n_adj_tiles, dp.abel_cluster_adj, g, nullptr, nullptr, st);
 }
 
+
+// ---------------------------------------------------------------------------
+// Fused time stage of the TV and primal-dual steps: radius sums M, forward
+// g = M P^T / K, residual, adjoint Mbar = r P, for kTimeJ detectors per
+// thread-block cluster of kTimeCS CTAs, in one launch.
+//
+// Every step is row-local (a detector's outputs need only that detector's
+// rows), so a cluster owns whole rows and nothing synchronises across the
+// grid:
+//   1. each CTA adds the circular-mean partial slots of its share of the
+//      radius chunks (in slot order, as k_msum) into its shared copy of M;
+//      cluster barrier; it copies the other shares from the other CTAs'
+//      shared memory, so each CTA holds the group's rows of M;
+//   2. forward: each CTA computes its time chunks of g and the residual
+//      r = g - data (or the dual update of y), kept in shared memory;
+//   3. cluster barrier; each CTA copies the other CTAs' residual chunks;
+//   4. adjoint: each CTA computes its radius chunks of Mbar.
+// Chunks of 32 outputs go to the ranks in boustrophedon order (0..7, 7..0,
+// 0..7, ...), which evens out the triangle of P (late forward chunks and
+// early adjoint chunks are the long ones).  The contraction of a chunk is
+// cut into blocks of 32 rows; warp w takes blocks w, w + 8, ... of each of
+// its CTA's chunks and walks them without CTA-wide synchronisation: a lane
+// owns one output for all 8 detectors (8 accumulators; a row's 8 detector
+// values are two broadcast 16-byte shared-memory loads), and the block's 32
+// values of P for that output sit in registers, loaded one block ahead
+// (the loads of the first block are issued before the dependency wait: P
+// does not depend on the data).  After a phase the warps' partial sums are
+// added in warp order (deterministic) and the epilogue runs.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kTimeThreads = kTimeWarps * kWarp;
+
+// chunk p of a rank (p = 0, 1, ...) and the rank that owns chunk c
+__device__ __forceinline__ int time_chunk(int p, int rank)
+{
+    return p * kTimeCS + ((p & 1) ? kTimeCS - 1 - rank : rank);
+}
+__device__ __forceinline__ int time_owner(int c)
+{
+    const int p = c / kTimeCS, r = c - p * kTimeCS;
+    return (p & 1) ? kTimeCS - 1 - r : r;
+}
+
+// Contraction blocks [lo, hi) (32 rows each) of output chunk c: forward chunk
+// c contracts radii [0, min(n_r, 32 c + 34)), adjoint chunk c times
+// [max(0, 32 c - 2), n_t) (P is zero elsewhere; the padded rows of P, P^T and
+// of the staged operands are zero).
+__device__ __forceinline__ void time_blocks(int phase, int c, int n_r, int n_tc, int& lo, int& hi)
+{
+    lo = phase == 0 ? 0 : max(0, 32 * c - 2) >> 5;
+    hi = phase == 0 ? (min(n_r, 32 * c + 34) + 31) >> 5 : n_tc;
+}
+
+struct TItem {
+    int phase;   // 0 forward, 1 adjoint
+    int p;       // the CTA's chunk index (slot of the partial sums)
+    int c;       // output chunk
+    int kc;      // contraction block
+    bool last;   // this warp's last block of the chunk
+};
+
+// The blocks of one warp: for each of its CTA's forward chunks, then each
+// adjoint chunk, blocks lo + w, lo + w + kTimeWarps, ... below hi.
+struct TWalk {
+    int phase = 0, p = 0, kc = -1;
+    int rank, w, n_tc, n_rc, n_r;
+    __device__ TWalk(int rank_, int w_, int n_tc_, int n_rc_, int n_r_)
+        : rank(rank_), w(w_), n_tc(n_tc_), n_rc(n_rc_), n_r(n_r_) {}
+    __device__ bool next(TItem& it)
+    {
+        for (;;) {
+            if (phase > 1) return false;
+            const int c = time_chunk(p, rank);
+            if (c >= (phase == 0 ? n_tc : n_rc)) {
+                ++phase;
+                p = 0;
+                kc = -1;
+                continue;
+            }
+            int lo, hi;
+            time_blocks(phase, c, n_r, n_tc, lo, hi);
+            const int k = kc < 0 ? lo + w : kc + kTimeWarps;
+            if (k >= hi) {
+                ++p;
+                kc = -1;
+                continue;
+            }
+            kc = k;
+            it.phase = phase;
+            it.p = p;
+            it.c = c;
+            it.kc = k;
+            it.last = k + kTimeWarps >= hi;
+            return true;
+        }
+    }
+};
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+} // namespace
+
+// DUAL = false: r = A f - g (y, if not null, receives r).
+// DUAL = true:  y <- (y + sigma (A f - g)) * inv1ps and r = the new y.
+template <bool DUAL>
+__global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const float* __restrict__ gdata,
+                                                              float* __restrict__ y, float sigma, float inv1ps)
+{
+    extern __shared__ __align__(16) unsigned char tp_smem[];
+    const int nch = dp.time_chunks;                                  // most chunks of a CTA in one phase
+    float* Ms = reinterpret_cast<float*>(tp_smem);                   // [radius][detector]
+    float* rs = Ms + (size_t)dp.time_rows_r * kTimeJ;                // [time][detector]
+    float* red = rs + (size_t)dp.time_rows_t * kTimeJ;               // [chunk p][warp][detector][lane]
+    float* gs = red + (size_t)nch * kTimeWarps * kTimeJ * kWarp;     // [chunk p][data, y][detector][lane]
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const TimeGroup grp = dp.time_groups[blockIdx.x / kTimeCS];
+    const InstDev in = dp.inst[grp.inst];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int n_tc = in.n_tp >> 5, n_rc = in.n_rp >> 5;
+    const float* PT = dp.P + in.p_off + (size_t)in.n_tp * in.n_rp + lane;   // P^T: row m, pitch n_tp
+    const float* PP = dp.P + in.p_off + lane;                               // P: row t, pitch n_rp
+
+    // this lane's 32 values of P for block it (output 32 c + lane, rows 32 kc ..)
+    auto load_block = [&](const TItem& it, float(&pv)[32]) {
+        const size_t pitch = it.phase == 0 ? in.n_tp : in.n_rp;
+        const float* src = (it.phase == 0 ? PT : PP) + 32 * it.c + (size_t)(32 * it.kc) * pitch;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) pv[r] = __ldg(src + r * pitch);
+    };
+    float acc[kTimeJ];
+#pragma unroll
+    for (int j = 0; j < kTimeJ; ++j) acc[j] = 0.f;
+    auto run_block = [&](const TItem& it, const float(&pv)[32]) {
+        const float* ab = (it.phase == 0 ? Ms : rs) + (size_t)(32 * it.kc) * kTimeJ;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const float4 a0 = *reinterpret_cast<const float4*>(ab + r * kTimeJ);
+            const float4 a1 = *reinterpret_cast<const float4*>(ab + r * kTimeJ + 4);
+            acc[0] = fmaf(pv[r], a0.x, acc[0]);
+            acc[1] = fmaf(pv[r], a0.y, acc[1]);
+            acc[2] = fmaf(pv[r], a0.z, acc[2]);
+            acc[3] = fmaf(pv[r], a0.w, acc[3]);
+            acc[4] = fmaf(pv[r], a1.x, acc[4]);
+            acc[5] = fmaf(pv[r], a1.y, acc[5]);
+            acc[6] = fmaf(pv[r], a1.z, acc[6]);
+            acc[7] = fmaf(pv[r], a1.w, acc[7]);
+        }
+        if (it.last) {   // this warp's partial sums of the chunk
+            float* dst = red + (size_t)((it.p * kTimeWarps + w) * kTimeJ) * kWarp + lane;
+#pragma unroll
+            for (int j = 0; j < kTimeJ; ++j) {
+                dst[j * kWarp] = acc[j];
+                acc[j] = 0.f;
+            }
+        }
+    };
+
+    TWalk walk(rank, w, n_tc, n_rc, in.n_r);
+    float pa[32], pb[32];
+    TItem cur, nxt;
+    bool have = walk.next(cur);
+    if (have) load_block(cur, pa);
+    bool in_b = false;   // the current block's values are in pb
+    // this warp's blocks of phase ph, the next block's loads in flight during each
+    auto run_phase = [&](int ph) {
+        while (have && cur.phase == ph) {
+            const bool more = walk.next(nxt);
+            if (!in_b) {
+                if (more) load_block(nxt, pb);
+                run_block(cur, pa);
+            } else {
+                if (more) load_block(nxt, pa);
+                run_block(cur, pb);
+            }
+            in_b = !in_b;
+            have = more;
+            cur = nxt;
+        }
+    };
+
+    pdl_wait();   // the partial slots come from the circular-mean kernel; g and y from earlier work
+
+    // the data (and y) of this CTA's time chunks, for the forward epilogue
+    for (int p = 0; time_chunk(p, rank) < n_tc; ++p) {
+        const int x = 32 * time_chunk(p, rank) + lane;
+        const bool ok = w < grp.jn && x < in.n_t;
+        const size_t o = ok ? in.g_off + (size_t)(grp.j0 + w) * in.n_t + x : 0;
+        float* d = gs + (size_t)(p * 2 * kTimeJ + w) * kWarp + lane;
+        cp_async4_zfill(d, gdata + o, ok);
+        if (DUAL) cp_async4_zfill(d + kTimeJ * kWarp, y + o, ok);
+    }
+    cp_async_commit();
+
+    // 1. M of this CTA's radius chunks: thread = (detector w, radius lane of the chunk),
+    //    kU chunks at a time with 8 slots of each in flight
+    {
+        constexpr int kU = 2;
+        const bool jok = w < grp.jn;
+        const int jj = grp.j0 + (jok ? w : 0);
+        const size_t plane = (size_t)in.n_det * in.n_r;
+        const float* src = dp.mpart + in.mpart_off + (size_t)jj * in.n_r;
+        const int32_t* cnt_row = reinterpret_cast<const int32_t*>(dp.slotcnt + in.slotcnt_off) + (size_t)jj * in.nmb;
+        for (int p0 = 0; time_chunk(p0, rank) < n_rc; p0 += kU) {
+            int m[kU], cnt[kU], cmax = 0;
+            float s[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int c = time_chunk(p0 + u, rank);
+                m[u] = 32 * c + lane;
+                cnt[u] = (c < n_rc && jok && m[u] < in.n_r) ? __ldg(cnt_row + m[u] / dp.m_lanes) : 0;
+                cmax = max(cmax, cnt[u]);
+                s[u] = 0.f;
+            }
+            for (int sl = 0; sl < cmax; sl += 8) {
+                float v[kU][8];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        v[u][k] = sl + k < cnt[u] ? __ldcg(src + (size_t)(sl + k) * plane + m[u]) : 0.f;
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (sl + k < cnt[u]) s[u] += v[u][k];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (time_chunk(p0 + u, rank) < n_rc) Ms[m[u] * kTimeJ + w] = s[u];
+        }
+    }
+    cluster_arrive();
+    cluster_wait();   // every CTA's share of M is in place
+    for (int idx = tid; idx < n_rc * 64; idx += kTimeThreads) {   // chunk c = float4s [64 c, 64 c + 64)
+        const int own = time_owner(idx >> 6);
+        if (own != rank)
+            reinterpret_cast<float4*>(Ms)[idx] = reinterpret_cast<const float4*>(cluster.map_shared_rank(Ms, own))[idx];
+    }
+    __syncthreads();
+
+    // 2. forward blocks, then the CTA's time chunks: g = sum / K and the residual
+    run_phase(0);
+    cp_async_wait_group<0>();   // this thread's data (and y) of its outputs
+    __syncthreads();            // every warp's partial sums are in place
+    for (int p = 0; time_chunk(p, rank) < n_tc; ++p) {   // thread = (detector w, output lane)
+        const int c = time_chunk(p, rank);
+        int lo, hi;
+        time_blocks(0, c, in.n_r, n_tc, lo, hi);
+        const int nw = min(kTimeWarps, hi - lo);   // warps that had blocks of this chunk
+        float sum = 0.f;
+        for (int ww = 0; ww < nw; ++ww) sum += red[(size_t)((p * kTimeWarps + ww) * kTimeJ + w) * kWarp + lane];
+        const int x = 32 * c + lane;
+        float r = 0.f;
+        if (w < grp.jn && x < in.n_t) {
+            const float* d = gs + (size_t)(p * 2 * kTimeJ + w) * kWarp + lane;
+            const size_t o = in.g_off + (size_t)(grp.j0 + w) * in.n_t + x;
+            const float g = sum * in.inv_K;
+            if (DUAL) {
+                r = fmaf(sigma, g - d[0], d[kTimeJ * kWarp]) * inv1ps;
+                y[o] = r;
+            } else {
+                r = g - d[0];
+                if (y) y[o] = r;
+            }
+        }
+        rs[x * kTimeJ + w] = r;   // zero for absent detectors and padded times
+    }
+
+    // 3. exchange of the residual chunks
+    cluster_arrive();
+    cluster_wait();   // every CTA's residual chunks are in place
+    for (int idx = tid; idx < n_tc * 64; idx += kTimeThreads) {
+        const int own = time_owner(idx >> 6);
+        if (own != rank)
+            reinterpret_cast<float4*>(rs)[idx] = reinterpret_cast<const float4*>(cluster.map_shared_rank(rs, own))[idx];
+    }
+    cluster_arrive();   // this CTA has read the others' shared memory (waited for at exit)
+    __syncthreads();    // the copies are visible to the CTA; the forward partial sums are consumed
+
+    // 4. adjoint blocks, then the CTA's radius chunks of Mbar
+    run_phase(1);
+    __syncthreads();
+    for (int p = 0; time_chunk(p, rank) < n_rc; ++p) {
+        const int c = time_chunk(p, rank);
+        int lo, hi;
+        time_blocks(1, c, in.n_r, n_tc, lo, hi);
+        const int nw = min(kTimeWarps, hi - lo);
+        float sum = 0.f;
+        for (int ww = 0; ww < nw; ++ww) sum += red[(size_t)((p * kTimeWarps + ww) * kTimeJ + w) * kWarp + lane];
+        const int x = 32 * c + lane;
+        if (w < grp.jn && x < in.n_r) dp.mbar[in.mbar_off + (size_t)(grp.j0 + w) * in.m_pitch + x] = sum;
+    }
+    cluster_wait();   // no CTA leaves while another may still read its shared memory
+}
+
+namespace {
+template <bool DUAL>
+cudaError_t launch_time_pair_t(const DevPlan& dp, const float* g, float* y, float sigma, float inv1ps,
+                               cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_time_pair<DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         dp.time_smem_bytes);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_time_pair<DUAL>, dim3((unsigned)(dp.n_time_groups * kTimeCS)), dim3(kTimeThreads),
+                      (size_t)dp.time_smem_bytes, st, kTimeCS, dp, g, y, sigma, inv1ps);
+}
+} // namespace
+
+cudaError_t launch_time_pair(const DevPlan& dp, const float* g, float* y, bool dual, float sigma, float inv1ps,
+                             cudaStream_t st)
+{
+    if (dp.n_time_groups == 0) return cudaSuccess;
+    if (dp.time_chunks <= 0) return cudaErrorInvalidValue;
+    return dual ? launch_time_pair_t<true>(dp, g, y, sigma, inv1ps, st)
+                : launch_time_pair_t<false>(dp, g, y, sigma, inv1ps, st);
+}
+
+int time_pair_clusters(int smem_bytes)
+{
+    const void* fn = reinterpret_cast<const void*>(k_time_pair<false>);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(kTimeCS);
+    cfg.blockDim = dim3(kTimeThreads);
+    cfg.dynamicSmemBytes = (size_t)smem_bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kTimeCS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 } // namespace patgpu

@@ -102,9 +102,9 @@ cudaError_t timed(Plan& p, int kind, cudaStream_t st, F&& fn)
 
 // The circular-mean launch; a wait probe armed by pat_plan_set_wait_probe
 // goes with this one launch only.
-cudaError_t circmean(Plan& p, const void* f, cudaStream_t st)
+cudaError_t circmean(Plan& p, const void* f, cudaStream_t st, bool msum = true)
 {
-    const cudaError_t e = launch_circmean(p.dp, f, st);
+    const cudaError_t e = launch_circmean(p.dp, f, st, msum);
     p.dp.wait_probe = 0;
     return e;
 }
@@ -158,6 +158,7 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
     if (opt.band_rows != 0 && (opt.band_rows < 1 || opt.band_rows > 8192)) return PAT_ERR_INVALID_ARG;
     if (opt.tile_cols != 0 && (opt.tile_cols < 1 || opt.tile_cols > 8192)) return PAT_ERR_INVALID_ARG;
     if (opt.adj_groups < 0 || opt.adj_groups > 16) return PAT_ERR_INVALID_ARG;
+    if (opt.time_pair != 0 && opt.time_pair != 1) return PAT_ERR_INVALID_ARG;
     if (opt.adj_mode < 0 || opt.adj_mode > 3) return PAT_ERR_INVALID_ARG;
     if (opt.abel_split != 0 && opt.abel_split != 1 && opt.abel_split != 2 && opt.abel_split != 4 &&
         opt.abel_split != 8)
@@ -331,10 +332,18 @@ pat_status_t pat_tv_step(pat_plan_t h, const float* d_f_in, float* d_f_out, cons
     if (!ds.ok) return PAT_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const DevPlan& dp = p->dp;
-    cudaError_t e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return circmean(*p, d_f_in, st); });
-    if (e == cudaSuccess)
-        e = timed(*p, PAT_K_ABEL_FWD, st, [&] { return launch_abel_fwd(dp, p->d_resid, st, d_g); });
-    if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, p->d_resid, st); });
+    const bool pair = dp.time_chunks > 0;
+    cudaError_t e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return circmean(*p, d_f_in, st, !pair); });
+    if (pair) {
+        if (e == cudaSuccess)
+            e = timed(*p, PAT_K_TIME_PAIR, st,
+                      [&] { return launch_time_pair(dp, d_g, nullptr, false, 0.f, 1.f, st); });
+    } else {
+        if (e == cudaSuccess)
+            e = timed(*p, PAT_K_ABEL_FWD, st, [&] { return launch_abel_fwd(dp, p->d_resid, st, d_g); });
+        if (e == cudaSuccess)
+            e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, p->d_resid, st); });
+    }
     if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return launch_adjoint_cells(dp, st); });
     if (e == cudaSuccess)
         e = timed(*p, PAT_K_TV_UPDATE, st,
@@ -387,10 +396,18 @@ pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, 
     const float inv1ps = 1.f / (1.f + sigma);
     cudaError_t e = timed(*p, PAT_K_PDHG_DUAL, st,
                           [&] { return launch_pdhg_dual_tv(dp, d_fbar, d_px, d_py, sigma, alpha, st); });
-    if (e == cudaSuccess) e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return circmean(*p, d_fbar, st); });
-    if (e == cudaSuccess)
-        e = timed(*p, PAT_K_ABEL_FWD, st, [&] { return launch_abel_fwd_dual(dp, d_y, d_g, sigma, inv1ps, st); });
-    if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, d_y, st); });
+    const bool pair = dp.time_chunks > 0;
+    if (e == cudaSuccess) e = timed(*p, PAT_K_CIRCMEAN, st, [&] { return circmean(*p, d_fbar, st, !pair); });
+    if (pair) {
+        if (e == cudaSuccess)
+            e = timed(*p, PAT_K_TIME_PAIR, st,
+                      [&] { return launch_time_pair(dp, d_g, d_y, true, sigma, inv1ps, st); });
+    } else {
+        if (e == cudaSuccess)
+            e = timed(*p, PAT_K_ABEL_FWD, st,
+                      [&] { return launch_abel_fwd_dual(dp, d_y, d_g, sigma, inv1ps, st); });
+        if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, d_y, st); });
+    }
     if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return launch_adjoint_cells(dp, st); });
     if (e == cudaSuccess)
         e = timed(*p, PAT_K_PDHG_PRIMAL, st,

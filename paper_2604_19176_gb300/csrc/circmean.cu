@@ -259,7 +259,7 @@ const void* circ_select(int ml, bool bf16)
 }
 } // namespace
 
-cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st)
+cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st, bool msum)
 {
     if (dp.n_fwd_ctas == 0) return cudaSuccess;
     const void* fn = circ_select(dp.m_lanes, dp.bf16 != 0);
@@ -279,7 +279,7 @@ cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st)
     const void* fptr = f;
     void* args[] = {&copy, &fptr};
     e = cudaLaunchKernelExC(&cfg, fn, args);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !msum) return e;
     return launch_pdl(k_msum, dim3((unsigned)dp.n_msum_rows, (unsigned)((dp.n_r_max + 127) / 128)), dim3(128), 0, st,
                       1, dp);
 }

@@ -39,9 +39,15 @@ cudaError_t launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem,
     return cudaLaunchKernelEx(&cfg, fn, static_cast<KArgs>(args)...);
 }
 
-cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st);
+cudaError_t launch_circmean(const DevPlan& dp, const void* f, cudaStream_t st, bool msum = true);
 cudaError_t launch_abel_fwd(const DevPlan& dp, float* g, cudaStream_t st, const float* gsub = nullptr);
 cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st);
+// Fused time stage (radius sums, forward, residual or dual update, adjoint)
+// of the steps: Mbar from the circular-mean partial slots in one launch.
+cudaError_t launch_time_pair(const DevPlan& dp, const float* g, float* y, bool dual, float sigma, float inv1ps,
+                             cudaStream_t st);
+// Clusters of the fused time stage that fit the GPU at once (0: cannot run).
+int time_pair_clusters(int smem_bytes);
 cudaError_t launch_adjoint_gather(const DevPlan& dp, void* f, cudaStream_t st);
 // Adjoint cell sums only (no combine), for the fused TV step.
 cudaError_t launch_adjoint_cells(const DevPlan& dp, cudaStream_t st);

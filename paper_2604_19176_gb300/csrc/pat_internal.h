@@ -95,6 +95,15 @@ struct TimeTile {
     int32_t inst, j0, x0, pad;
 };
 
+// Group of the fused time stage (k_time_pair): detectors [j0, j0 + jn) of
+// instance inst, jn <= kTimeJ, processed by one cluster of kTimeCS CTAs.
+struct TimeGroup {
+    int32_t inst, j0, jn, pad;
+};
+constexpr int kTimeJ = 8;          // detectors per fused time group
+constexpr int kTimeCS = 8;         // CTAs per cluster of the fused time stage
+constexpr int kTimeWarps = 8;      // warps per fused time CTA (one detector each in the epilogues)
+
 // Adjoint cell item of instance inst: in enumeration mode the 8 x 4 patch of
 // cells with lower-left cell (x0, y0) (absolute indices, >= -1) for detectors
 // j = group (mod G); in list mode the 2 x 2 block of cells at (x0, y0).
@@ -130,6 +139,7 @@ struct DevPlan {
     const TimeTile* adj_tiles;
     const CellItem* cell_items;
     const ImgTile* img_tiles;
+    const TimeGroup* time_groups;  // fused time stage groups, most work first
     const int64_t* cell_start;     // adjoint lists: first entry of each cell (see kListPad)
     const uint32_t* codes;         // adjoint lists: packed (q, j, m) codes, or weight indices j * m_pitch + m
     const float* frac_a;           // fraction lists: the FP32 fractions a, b of every entry
@@ -156,6 +166,11 @@ struct DevPlan {
     int32_t abel_cluster_fwd;      // CTAs per cluster splitting each forward time contraction
     int32_t abel_cluster_adj;      // the same for the adjoint time contraction
     int32_t bf16;                  // image storage is BF16
+    int32_t n_time_groups;
+    int32_t time_chunks;           // fused time stage: most output chunks of a CTA in one phase; 0 = not used
+    int32_t time_rows_r;           // largest n_rp: rows of M staged per fused time CTA
+    int32_t time_rows_t;           // largest n_tp: rows of the residual staged per fused time CTA
+    int32_t time_smem_bytes;       // dynamic shared memory of the fused time stage
 };
 
 constexpr int kAbelJ = 32;         // detectors per Abel tile (4 per warp)

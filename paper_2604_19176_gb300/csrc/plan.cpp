@@ -678,6 +678,29 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                      [&](const TimeTile& a, const TimeTile& b) { return fwd_len(a) > fwd_len(b); });
     std::stable_sort(adj_tiles.begin(), adj_tiles.end(),
                      [&](const TimeTile& a, const TimeTile& b) { return adj_len(a) > adj_len(b); });
+    // fused time stage of the steps: one cluster per kTimeJ detectors (largest
+    // n_t first); shared memory per CTA: the group's rows of M and of the
+    // residual, the warps' partial sums and the data of its time chunks
+    std::vector<TimeGroup> tgroups;
+    int time_rows_r = 0, time_rows_t = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const InstDev& d = inst[i];
+        for (int j0 = 0; j0 < d.n_det; j0 += kTimeJ) tgroups.push_back({i, j0, std::min(kTimeJ, d.n_det - j0), 0});
+        time_rows_r = std::max(time_rows_r, d.n_rp);
+        time_rows_t = std::max(time_rows_t, d.n_tp);
+    }
+    std::stable_sort(tgroups.begin(), tgroups.end(),
+                     [&](const TimeGroup& a, const TimeGroup& b) { return inst[a.inst].n_t > inst[b.inst].n_t; });
+    int time_chunks = 0, time_smem = 0;
+    if (opt.time_pair == 0) {
+        const int chunks = (time_rows_r / 32 + kTimeCS - 1) / kTimeCS;   // n_rc >= n_tc
+        const int64_t bytes = (int64_t)(time_rows_r + time_rows_t) * kTimeJ * 4 +
+                              (int64_t)chunks * (kTimeWarps + 2) * kTimeJ * kWarp * 4;
+        if (bytes <= P.max_smem_optin && time_pair_clusters((int)bytes) > 0) {
+            time_chunks = chunks;
+            time_smem = (int)bytes;
+        }
+    }
     // with fewer tiles than SMs, a cluster of CTAs splits each contraction
     auto cluster_for = [&](size_t tiles) {
         if (opt.abel_split > 0) return (int)opt.abel_split;
@@ -707,6 +730,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const size_t o_at = reserve(sizeof(TimeTile) * adj_tiles.size());
     const size_t o_ci = reserve(sizeof(CellItem) * citems.size());
     const size_t o_it = reserve(sizeof(ImgTile) * itiles.size());
+    const size_t o_tg = reserve(sizeof(TimeGroup) * tgroups.size());
     const size_t o_status = reserve(64);
     const size_t o_count = reserve(64);
     P.tables_bytes = off;
@@ -734,6 +758,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     put(o_at, adj_tiles.data(), sizeof(TimeTile) * adj_tiles.size());
     put(o_ci, citems.data(), sizeof(CellItem) * citems.size());
     put(o_it, itiles.data(), sizeof(ImgTile) * itiles.size());
+    put(o_tg, tgroups.data(), sizeof(TimeGroup) * tgroups.size());
     if (cudaMemcpyAsync(P.d_tables, host.data(), P.tables_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return PAT_ERR_CUDA;
 
@@ -777,6 +802,12 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     dp.adj_tiles = reinterpret_cast<const TimeTile*>(base + o_at);
     dp.cell_items = reinterpret_cast<const CellItem*>(base + o_ci);
     dp.img_tiles = reinterpret_cast<const ImgTile*>(base + o_it);
+    dp.time_groups = reinterpret_cast<const TimeGroup*>(base + o_tg);
+    dp.n_time_groups = (int32_t)tgroups.size();
+    dp.time_chunks = time_chunks;
+    dp.time_rows_r = time_rows_r;
+    dp.time_rows_t = time_rows_t;
+    dp.time_smem_bytes = time_smem;
     dp.mpart = P.d_work;
     dp.msum = P.d_work + o_msum;
     dp.mbar = P.d_work + o_mbar;
@@ -959,6 +990,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     I.adj_mode = dp.adj_mode == 0 ? 2 : dp.adj_mode;
     I.abel_split_fwd = dp.abel_cluster_fwd;
     I.abel_split_adj = dp.abel_cluster_adj;
+    I.time_pair = dp.time_chunks > 0 ? 1 : 0;
     I.list_bytes = list_bytes;
     I.device_bytes += list_bytes;
     I.bands_max = tiles_max;

@@ -219,10 +219,12 @@ def test_plan_errors(cuda_dev):
 
 
 def test_fused_tv_step_matches_separate_calls(cuda_dev):
-    """pat_tv_step equals pat_forward, pat_residual, pat_adjoint, pat_tv_grad
-    and pat_descent_step in sequence (same arithmetic, fewer kernels)."""
+    """pat_tv_step with separate time-stage launches (time_pair = 1) equals
+    pat_forward, pat_residual, pat_adjoint, pat_tv_grad and pat_descent_step
+    in sequence (same arithmetic, fewer kernels).  The fused time stage sums
+    its contractions in another order: tests/test_gpu_time_pair.py."""
     g = Geometry(64, 32, 0.2, math.pi, 96, 2.0, 128)
-    plan = PatPlan(g, device=cuda_dev)
+    plan = PatPlan(g, device=cuda_dev, time_pair=1)
     f0 = torch.tensor(np.abs(inputs.random_image(64, seed=41)), dtype=torch.float32, device=cuda_dev)
     data = torch.tensor(inputs.random_data(32, 96, seed=42), dtype=torch.float32, device=cuda_dev)
     tau, lam, eps = 0.05, 0.3, 1e-2
