@@ -18,8 +18,9 @@
 //   code lists (the default when 4 B per sample fits the list budget and a
 //     (q, j, m) code fits 32 bits): at plan creation the enumeration runs
 //     twice (count, then fill) to store every cell's hits as packed codes,
-//     each cell's list contiguous; each call streams the lists and recomputes
-//     a and b from the codes with the forward's expressions (k_adj_list).
+//     the 32 cells of an 8 x 4 patch interleaved vector by vector so that a
+//     warp streams them with full 512-byte loads; each call recomputes a and b
+//     from the codes with the forward's expressions (k_adj_list).
 //   fraction lists (12 B per sample): the hits as (Mbar index, a, b), a and b
 //     the exact FP32 values the forward computes (one table load per sample,
 //     no coordinate arithmetic, but a 3x larger stream).
@@ -146,67 +147,75 @@ __global__ void __launch_bounds__(256, 5) k_adj_cells(DevPlan dp)
 // ---------------------------------------------------------------------------
 // List building (plan creation): count (MODE 0), then fill, the hits of every
 // cell of instance `inst_idx`, all detectors, in enumeration order.  Thread =
-// cell; cell c writes entries start[c] .. start[c + 1] - 1 (its hits, then
-// null entries up to the padded length, see kListPad).  MODE 1: packed codes
-// q << (jb + mb) | j << mb | m; MODE 2: weight index j * m_pitch + m and the
-// fractions a, b.
+// cell.  MODE 1: packed codes q << (jb + mb) | j << mb | m; MODE 2: the Mbar
+// index j * m_pitch + m and the fractions a, b.  Entry k of a cell goes to
+// vector k / 4 of the part that holds that vector, component k % 4, then
+// null entries fill the last vector (layout in pat_internal.h).
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int32_t* __restrict__ counts,
-                                                   const int64_t* __restrict__ start, uint32_t* __restrict__ out,
-                                                   float* __restrict__ fa, float* __restrict__ fb)
+                                                   const int64_t* __restrict__ pbase, uint32_t* __restrict__ out)
 {
     const InstDev in = dp.inst[inst_idx];
     const int n = in.n, w = n + 1;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= w * w) return;
-    const int cx = idx % w - 1, cy = idx / w - 1;
-    const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
+    const int cxa = idx % w, cya = idx / w;   // cell index + 1
+    const float cxf = (float)(cxa - 1 - in.c0), cyf = (float)(cya - 1 - in.c0);
     const int mb = in.code_mbits, jmb = in.code_jbits + in.code_mbits;
-    int64_t o = 0, len = 0;
+    const int G = dp.adj_groups;
+    constexpr int S = MODE == 2 ? 3 : 1;   // 16-byte slots per vector
+    int count = 0, nv = 0, lane = 0;
+    const int64_t* pb = nullptr;
     if (MODE) {
-        o = start[idx];
-        len = start[idx + 1] - o;
+        count = counts[idx];
+        nv = (count + 3) >> 2;
+        pb = pbase + ((int64_t)(cya / kPatchH) * in.patches_x + cxa / kPatchW) * G;
+        lane = (cya % kPatchH) * kPatchW + cxa % kPatchW;
     }
-    int64_t k = 0;
+    // part g holds vectors [v0, v1) = [g nv / G, (g + 1) nv / G); entries come in order
+    int g = 0, v0 = 0, v1 = MODE ? nv / G : 0;
+    auto put = [&](int k, uint32_t code, float a, float b) {
+        const int v = k >> 2;
+        while (v >= v1) {
+            ++g;
+            v0 = v1;
+            v1 = (int)((int64_t)(g + 1) * nv / G);
+        }
+        const int64_t slot = pb[g] + (int64_t)(v - v0) * S * kWarp + lane;
+        const int c = k & 3;
+        out[slot * 4 + c] = code;
+        if (MODE == 2) {
+            out[(slot + kWarp) * 4 + c] = __float_as_uint(a);
+            out[(slot + 2 * kWarp) * 4 + c] = __float_as_uint(b);
+        }
+    };
+    int k = 0;
     enumerate_cell(dp, in, cxf, cyf, 0, 1, [&](int j, int m, int q, float a, float b) {
-        if (MODE && k < len) {   // (the fill sees exactly the counted hits; never write past them)
+        if (MODE && k < count) {   // (the fill sees exactly the counted hits; never write past them)
             const uint32_t widx = ((uint32_t)j << mb) | (uint32_t)m;
-            if (MODE == 1) {
-                out[o + k] = ((uint32_t)q << jmb) | widx;
-            } else {
-                out[o + k] = widx;
-                fa[o + k] = a;
-                fb[o + k] = b;
-            }
+            put(k, MODE == 1 ? (((uint32_t)q << jmb) | widx) : widx, a, b);
         }
         ++k;
     });
     if (!MODE) {
-        counts[idx] = (int32_t)k;
+        counts[idx] = k;
         return;
     }
     const uint32_t null_widx = (uint32_t)in.m_pitch - 1u;   // row 0, a column that is always zero
-    for (; k < len; ++k) {
-        out[o + k] = null_widx;   // (q = 0 for codes)
-        if (MODE == 2) {
-            fa[o + k] = 0.f;
-            fb[o + k] = 0.f;
-        }
-    }
+    for (int kk = count; kk < 4 * nv; ++kk) put(kk, null_widx, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
-// List mode: one warp per 2 x 2 block of cells; lanes 8 g .. 8 g + 7 share
-// cell g's list, lane l taking entries l, l + 8, l + 16, ... (all four lists
-// are walked in step, so at any time the warp reads neighbouring cells'
-// samples at similar list positions: nearby detectors, rays and Mbar
-// entries).  Each lane accumulates the moments sum w, sum w a, sum w b,
-// sum w a b of its entries (w = Mbar[j][m]; a, b recomputed from the code
-// exactly as the forward computes them, or stored), the eight lanes' moments
-// are added by a fixed shuffle tree, and the cell's four corner sums
+// List mode: lane = cell of an 8 x 4 patch, warp = (patch, part) item.  Each
+// lane streams its cell's part as 16-byte vectors (a warp's load is 512
+// contiguous bytes: the 32 cells' vectors are interleaved), four vectors in
+// flight, and accumulates the moments sum w, sum w a, sum w b, sum w a b of
+// its entries (w = Mbar[j][m]; a and b recomputed from the code exactly as
+// the forward computes them, or stored); null entries have w = 0.  The
+// cell's four corner sums
 //     Z00 = sum w (1-a)(1-b), Z10 = sum w a (1-b), Z01 = sum w (1-a) b, Z11 = sum w a b
-// are written once per cell (no atomics, deterministic).
+// go to plane `part` of Z, each written once (no atomics, deterministic).
 // ---------------------------------------------------------------------------
 namespace {
 struct Moments {
@@ -222,69 +231,61 @@ struct Moments {
 };
 } // namespace
 
-namespace {
-// The list range of the cell that lane group `grp` owns in 2 x 2 block `it`.
-__device__ __forceinline__ bool item_cell(const DevPlan& dp, const CellItem& it, int grp, int& n, int& cell,
-                                          int64_t& beg, int& len)
-{
-    const InstDev& in = dp.inst[it.inst];
-    n = in.n;
-    const int cx = it.x0 + (grp & 1), cy = it.y0 + (grp >> 1);
-    if (cx > n - 1 || cy > n - 1) {
-        beg = 0;
-        len = 0;
-        return false;
-    }
-    cell = (cy + 1) * (n + 1) + (cx + 1);
-    const int64_t* st = dp.cell_start + in.list_off + cell;
-    beg = st[0];
-    len = (int)(st[1] - beg);
-    return true;
-}
-} // namespace
-
 template <bool FRAC>
 __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
 {
     pdl_wait();   // Mbar comes from the previous kernel; the queue from earlier calls
-    constexpr int U = 4;   // entries per lane per block: a block is U * kListPad entries of a cell
-    const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
+    const int lane = threadIdx.x & 31;
     int32_t* ctr = dp.work_counters + kQueueStride;
-    int item = take_item(ctr, lane);
-    while (item < dp.n_list_items) {
-        // take the next item now and prefetch its lists into L2 while this one runs
-        const int next = take_item(ctr, lane);
-        if (next < dp.n_list_items && gl == 0) {
-            int nn, ncell, nlen;
-            int64_t nbeg;
-            if (item_cell(dp, dp.list_items[next], grp, nn, ncell, nbeg, nlen) && nlen > 0) {
-                prefetch_l2(dp.codes + nbeg, 4u * (uint32_t)nlen);   // 32-byte aligned: kListPad entries
-                if (FRAC) {
-                    prefetch_l2(dp.frac_a + nbeg, 4u * (uint32_t)nlen);
-                    prefetch_l2(dp.frac_b + nbeg, 4u * (uint32_t)nlen);
-                }
-            }
-        }
+    const int G = dp.adj_groups;
+    for (;;) {
+        const int item = take_item(ctr, lane);
+        if (item >= dp.n_list_items) break;
         const CellItem it = dp.list_items[item];
         const InstDev in = dp.inst[it.inst];
-        int n, cell, len;
-        int64_t beg;
-        const bool cell_ok = item_cell(dp, it, grp, n, cell, beg, len);
-        const int cx = it.x0 + (grp & 1), cy = it.y0 + (grp >> 1);
-        const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
+        const int n = in.n, w = n + 1;
+        const int cx = it.x0 + (lane & (kPatchW - 1)), cy = it.y0 + lane / kPatchW;
+        if (cx > n - 1 || cy > n - 1) continue;
+        const int cell = (cy + 1) * w + (cx + 1);
+        const int nv = (dp.cell_cnt[in.list_off + cell] + 3) >> 2;
+        const int v0 = (int)((int64_t)it.group * nv / G);
+        const int nk = (int)((int64_t)(it.group + 1) * nv / G) - v0;
+        const int64_t pbi =
+            in.pbase_off + ((int64_t)((it.y0 + 1) / kPatchH) * in.patches_x + (it.x0 + 1) / kPatchW) * G + it.group;
+        const uint4* L = reinterpret_cast<const uint4*>(dp.codes) + dp.list_base[pbi] + lane;
         const float* mb = dp.mbar + in.mbar_off;
-        const float4* det = dp.det + in.det_off;
-        const float4* rays = dp.rays + in.ray_off;
-        const uint32_t wmask = (1u << (in.code_jbits + in.code_mbits)) - 1u, mmask = (1u << in.code_mbits) - 1u;
-        const int qshift = in.code_jbits + in.code_mbits, mbits = in.code_mbits;
-        const uint32_t* cp = dp.codes + beg + gl;
-        const float* ap = FRAC ? dp.frac_a + beg + gl : nullptr;
-        const float* bp = FRAC ? dp.frac_b + beg + gl : nullptr;
         Moments acc;
-        auto entry = [&](uint32_t c, float fa, float fb) {
-            if (FRAC) {
-                acc.add(__ldg(mb + c), fa, fb);
-            } else {
+        if constexpr (FRAC) {
+            // two vectors (8 entries) in flight per lane
+            for (int kb = 0; kb < nk; kb += 2) {
+                uint4 ci[2], ca[2], cb[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (kb + u < nk) {
+                        const uint4* p = L + (size_t)(kb + u) * 3 * kWarp;
+                        ci[u] = __ldcs(p);
+                        ca[u] = __ldcs(p + kWarp);
+                        cb[u] = __ldcs(p + 2 * kWarp);
+                    } else {
+                        ci[u] = ca[u] = cb[u] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (kb + u >= nk) break;
+                    acc.add(__ldg(mb + ci[u].x), __uint_as_float(ca[u].x), __uint_as_float(cb[u].x));
+                    acc.add(__ldg(mb + ci[u].y), __uint_as_float(ca[u].y), __uint_as_float(cb[u].y));
+                    acc.add(__ldg(mb + ci[u].z), __uint_as_float(ca[u].z), __uint_as_float(cb[u].z));
+                    acc.add(__ldg(mb + ci[u].w), __uint_as_float(ca[u].w), __uint_as_float(cb[u].w));
+                }
+            }
+        } else {
+            const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
+            const float4* det = dp.det + in.det_off;
+            const float4* rays = dp.rays + in.ray_off;
+            const int mbits = in.code_mbits, qshift = in.code_jbits + in.code_mbits;
+            const uint32_t wmask = (1u << qshift) - 1u, mmask = (1u << mbits) - 1u;
+            auto entry = [&](uint32_t c) {
                 const uint32_t widx = c & wmask;
                 const int q = (int)(c >> qshift), j = (int)(widx >> mbits);
                 const float mf = __uint_as_float((c & mmask) | kMagicBits) - kMagic;   // m < 2^22
@@ -294,68 +295,25 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
                 // the sample lies in this cell: its relative cell is (cxf, cyf) - floor(U, V)
                 const float cxr = __fsub_rn(cxf, d.x), cyr = __fsub_rn(cyf, d.y);
                 acc.add(wv, cell_frac(mf, r.x, r.z, d.z, cxr), cell_frac(mf, r.y, r.w, d.w, cyr));
-            }
-        };
-        // full blocks of U entries per lane, the next block's loads in flight
-        // while this one is processed; then at most U - 1 single entries
-        constexpr int BS = U * kListPad;
-        const int nblk = len / BS, tail = (len - nblk * BS) / kListPad;
-        uint32_t c[U], cn[U];
-        float fa[U], fb[U], fan[U], fbn[U];
+            };
+            // four vectors in flight per lane, then their 16 entries
+            for (int kb = 0; kb < nk; kb += 4) {
+                uint4 c[4];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            c[u] = 0u;
-            fa[u] = fb[u] = 0.f;
-        }
-        if (nblk > 0) {
+                for (int u = 0; u < 4; ++u)
+                    c[u] = (kb + u < nk) ? __ldcs(L + (size_t)(kb + u) * kWarp) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                c[u] = __ldcs(cp + u * kListPad);
-                if (FRAC) {
-                    fa[u] = __ldcs(ap + u * kListPad);
-                    fb[u] = __ldcs(bp + u * kListPad);
+                for (int u = 0; u < 4; ++u) {
+                    if (kb + u >= nk) break;
+                    entry(c[u].x);
+                    entry(c[u].y);
+                    entry(c[u].z);
+                    entry(c[u].w);
                 }
             }
         }
-        for (int b = 0; b < nblk; ++b) {
-            const int o = (b + 1) * BS;
-            if (b + 1 < nblk) {
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    cn[u] = __ldcs(cp + o + u * kListPad);
-                    if (FRAC) {
-                        fan[u] = __ldcs(ap + o + u * kListPad);
-                        fbn[u] = __ldcs(bp + o + u * kListPad);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) entry(c[u], fa[u], fb[u]);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                c[u] = cn[u];
-                if (FRAC) {
-                    fa[u] = fan[u];
-                    fb[u] = fbn[u];
-                }
-            }
-        }
-        for (int t = 0; t < tail; ++t) {
-            const int o = nblk * BS + t * kListPad;
-            entry(__ldcs(cp + o), FRAC ? __ldcs(ap + o) : 0.f, FRAC ? __ldcs(bp + o) : 0.f);
-        }
-#pragma unroll
-        for (int o = kListPad / 2; o > 0; o >>= 1) {
-            acc.s0 += __shfl_xor_sync(0xffffffffu, acc.s0, o);
-            acc.sa += __shfl_xor_sync(0xffffffffu, acc.sa, o);
-            acc.sb += __shfl_xor_sync(0xffffffffu, acc.sb, o);
-            acc.sab += __shfl_xor_sync(0xffffffffu, acc.sab, o);
-        }
-        if (gl == 0 && cell_ok) {
-            const float z10 = acc.sa - acc.sab, z01 = acc.sb - acc.sab;
-            dp.zbuf[in.z_off + cell] = make_float4(acc.s0 - acc.sa - z01, z10, z01, acc.sab);
-        }
-        item = next;
+        const float z10 = acc.sa - acc.sab, z01 = acc.sb - acc.sab;
+        dp.zbuf[in.z_off + (size_t)it.group * w * w + cell] = make_float4(acc.s0 - acc.sa - z01, z10, z01, acc.sab);
     }
     release_queue(ctr, lane);
 }
@@ -402,14 +360,14 @@ int adj_list_blocks_per_sm(bool frac)
     return nb;
 }
 
-cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* start,
-                             uint32_t* out, float* fa, float* fb, cudaStream_t st)
+cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
+                             uint32_t* out, bool frac, cudaStream_t st)
 {
     const int cells = (n + 1) * (n + 1);
     const int blocks = (cells + 255) / 256;
-    if (!out) k_adj_build<0><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, start, out, fa, fb);
-    else if (fa) k_adj_build<2><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, start, out, fa, fb);
-    else k_adj_build<1><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, start, out, fa, fb);
+    if (!out) k_adj_build<0><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
+    else if (frac) k_adj_build<2><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
+    else k_adj_build<1><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
     return cudaGetLastError();
 }
 

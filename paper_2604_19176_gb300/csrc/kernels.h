@@ -87,7 +87,7 @@ int adj_list_blocks_per_sm(bool frac);
 // padded list starts `start` (entries), fills the lists as packed codes
 // (4 B per entry) or, with fa / fb, as weight indices plus the fractions
 // a, b (12 B per entry).
-cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* start,
-                             uint32_t* out, float* fa, float* fb, cudaStream_t st);
+cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
+                             uint32_t* out, bool frac, cudaStream_t st);
 
 } // namespace patgpu

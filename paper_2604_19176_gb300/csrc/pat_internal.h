@@ -57,13 +57,14 @@ struct InstDev {
     int64_t slotcnt_off;           // byte offset of the slot counts (n_det x nmb int32)
     int64_t z_off;                 // float4 offset of the adjoint cell sums (groups x (n+1)^2)
     int64_t ray_off;               // entry offset of the instance's 2K rays and reciprocal rays
-    int64_t list_off;              // adjoint lists: offset of the instance's (n+1)^2 + 1 cell starts
+    int64_t list_off;              // adjoint lists: offset of the instance's (n+1)^2 cell counts
+    int64_t pbase_off;             // adjoint lists: offset of the instance's (patch, part) block bases
     int32_t code_jbits, code_mbits; // adjoint list mode: code = q << (jb+mb) | j << mb | m
     int32_t n_rp;                  // row pitch (multiple of 32) of P
     int32_t n_tp;                  // row pitch (multiple of 32) of P^T
     int32_t m_pitch;               // row pitch of M and Mbar: a power of two > n_r (the columns from
                                    //   n_r on stay zero), so a list code's low bits are j * m_pitch + m
-    int32_t pad2;
+    int32_t patches_x;             // adjoint lists: 8 x 4 cell patches per row of cells
 };
 
 // Circular-mean work unit: radii [m0, m0 + m_lanes) of detector j, angles
@@ -104,18 +105,21 @@ constexpr int kTimeJ = 8;          // detectors per fused time group
 constexpr int kTimeCS = 8;         // CTAs per cluster of the fused time stage
 constexpr int kTimeWarps = 8;      // warps per fused time CTA (one detector each in the epilogues)
 
-// Adjoint cell item of instance inst: in enumeration mode the 8 x 4 patch of
-// cells with lower-left cell (x0, y0) (absolute indices, >= -1) for detectors
-// j = group (mod G); in list mode the 2 x 2 block of cells at (x0, y0).
+// Adjoint cell item of instance inst: the 8 x 4 patch of cells with
+// lower-left cell (x0, y0) (absolute indices, >= -1); in enumeration mode for
+// detectors j = group (mod G), in list mode part `group` of the cells' lists.
 struct CellItem {
     int32_t inst, x0, y0, group;
 };
 
 // Adjoint lists.  Cell c of an instance (cells numbered (cy + 1) * (n + 1) +
-// cx + 1) owns entries [start[c], start[c + 1]) of the list arrays: its
-// samples in the order (j, q, m), padded with null entries (weight index of
-// the always-zero column m_pitch - 1 of row 0) to a multiple of kListPad.
-constexpr int kListPad = 8;        // lanes per cell in the list gather
+// cx + 1) has count[c] samples in the order (j, q, m), grouped in vectors of
+// four (the last one padded with null entries: weight index of the
+// always-zero column m_pitch - 1 of row 0) and split into G parts of
+// consecutive vectors.  Part g of the 32 cells of an 8 x 4 patch is one block
+// of 16-byte slots: vector k of the cell in lane l at slot base + k * 32 + l
+// (code lists), or base + (3 k + s) * 32 + l for fraction lists (s = 0: Mbar
+// indices, 1: a, 2: b), each block as long as the patch's longest part.
 
 // Tile of the elementwise / stencil kernels: 32 x 8 pixels.
 struct ImgTile {
@@ -140,11 +144,10 @@ struct DevPlan {
     const CellItem* cell_items;
     const ImgTile* img_tiles;
     const TimeGroup* time_groups;  // fused time stage groups, most work first
-    const int64_t* cell_start;     // adjoint lists: first entry of each cell (see kListPad)
-    const uint32_t* codes;         // adjoint lists: packed (q, j, m) codes, or weight indices j * m_pitch + m
-    const float* frac_a;           // fraction lists: the FP32 fractions a, b of every entry
-    const float* frac_b;
-    const CellItem* list_items;    // adjoint list mode: 2 x 2 cell blocks, longest lists first
+    const int64_t* list_base;      // adjoint lists: first 16-byte slot of each (patch, part) block
+    const int32_t* cell_cnt;       // adjoint lists: samples of each cell
+    const uint32_t* codes;         // adjoint lists: the blocks (codes, or indices and fractions)
+    const CellItem* list_items;    // adjoint list mode: (patch, part) items, longest part first
     float* mpart;                  // forward partial slots
     float* msum;                   // forward circular-mean sums M (same layout as Mbar)
     int32_t* work_counters;        // dynamic work queues, kQueueStride ints apart (see kQueueStride)

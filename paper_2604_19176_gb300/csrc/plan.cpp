@@ -622,7 +622,17 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             }
     }
     std::stable_sort(wit.begin(), wit.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    const int ZG = use_lists ? 1 : AG;   // list mode writes one corner-sum plane
+    // list mode: each cell's list is cut into LG parts (one corner-sum plane
+    // each), enough (patch, part) items for about two per resident warp
+    int LG = 1;
+    if (use_lists) {
+        const int lbps = adj_list_blocks_per_sm(frac_lists);
+        if (lbps < 1) return PAT_ERR_UNSUPPORTED;
+        const int64_t lres = (int64_t)lbps * P.num_sms * 8;
+        LG = opt.adj_groups > 0 ? opt.adj_groups
+                                : (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * lres + patches - 1) / patches));
+    }
+    const int ZG = use_lists ? LG : AG;
     std::vector<CellItem> citems;
     citems.reserve(wit.size());
     for (auto& w : wit) citems.push_back(w.second);
@@ -857,10 +867,14 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     }
 
     // ---- adjoint sample lists (list mode) --------------------------------------
-    // Hits are counted per cell, then stored per cell, contiguous, padded
-    // to kListPad entries (see pat_internal.h and k_adj_build).
+    // Hits are counted per cell, then stored per (8 x 4 patch, part): the 32
+    // cells' parts interleaved vector by vector, each block as long as the
+    // patch's longest part (layout in pat_internal.h, fill in k_adj_build).
     int64_t list_bytes = 0;
     if (use_lists) {
+        const int S = frac_lists ? 3 : 1;     // 16-byte slots per vector of four entries
+        const int G = LG;
+        dp.adj_groups = G;                    // the fill kernel splits lists into G parts
         // count the hits of every cell, per geometry template (first instance)
         std::vector<int> rep(tmpls.size(), -1);
         for (int i = 0; i < n_inst; ++i)
@@ -878,7 +892,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
             const int i = rep[t];
             const int cells = (inst[i].n + 1) * (inst[i].n + 1);
-            if (launch_adj_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, nullptr, nullptr, st) != cudaSuccess)
+            if (launch_adj_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, false, st) != cudaSuccess)
                 s = PAT_ERR_CUDA;
             counts[t].resize(cells);
             if (s == PAT_OK && cudaMemcpyAsync(counts[t].data(), d_counts, sizeof(int32_t) * cells,
@@ -888,43 +902,59 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         }
         cudaFree(d_counts);
         if (s != PAT_OK) return s;
-        // cell starts per template (padded lengths), one extra entry each
-        std::vector<int64_t> start_all;
-        std::vector<int64_t> tmpl_start_off(tmpls.size());
-        std::vector<std::vector<int32_t>> padded(tmpls.size());
-        int64_t entries = 0;
+        // block bases per (template, patch, part) and the longest part of each
+        std::vector<int32_t> cnt_all;
+        std::vector<int64_t> pbase_all;
+        std::vector<int64_t> tmpl_cnt_off(tmpls.size()), tmpl_pbase_off(tmpls.size());
+        std::vector<std::vector<int32_t>> part_len(tmpls.size());
+        int64_t slots_total = 0;   // 16-byte slots
         for (size_t t = 0; t < tmpls.size(); ++t) {
-            tmpl_start_off[t] = (int64_t)start_all.size();
-            padded[t].resize(counts[t].size());
-            for (size_t c = 0; c < counts[t].size(); ++c) {
-                padded[t][c] = (counts[t][c] + kListPad - 1) / kListPad * kListPad;
-                start_all.push_back(entries);
-                entries += padded[t][c];
-            }
-            start_all.push_back(entries);
+            const int n = inst[rep[t]].n, w = n + 1;
+            const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
+            tmpl_cnt_off[t] = (int64_t)cnt_all.size();
+            cnt_all.insert(cnt_all.end(), counts[t].begin(), counts[t].end());
+            tmpl_pbase_off[t] = (int64_t)pbase_all.size();
+            part_len[t].assign((size_t)pw * ph * G, 0);
+            for (int py = 0; py < ph; ++py)
+                for (int px = 0; px < pw; ++px)
+                    for (int g = 0; g < G; ++g) {
+                        int V = 0;
+                        for (int dy = 0; dy < kPatchH; ++dy)
+                            for (int dx = 0; dx < kPatchW; ++dx) {
+                                const int cxa = px * kPatchW + dx, cya = py * kPatchH + dy;   // cell + 1
+                                if (cxa >= w || cya >= w) continue;
+                                const int nv = (counts[t][(size_t)cya * w + cxa] + 3) >> 2;
+                                const int v0 = (int)((int64_t)g * nv / G), v1 = (int)((int64_t)(g + 1) * nv / G);
+                                V = std::max(V, v1 - v0);
+                            }
+                        part_len[t][((size_t)py * pw + px) * G + g] = V;
+                        pbase_all.push_back(slots_total);
+                        slots_total += (int64_t)V * S * kWarp;
+                    }
+            for (int i = 0; i < n_inst; ++i)
+                if (inst_tmpl[i] == (int)t) inst[i].patches_x = pw;
         }
-        // work items: 2 x 2 cell blocks, longest list first
+        // work items: (patch, part), longest part first
         std::vector<std::pair<int32_t, CellItem>> li;
         for (int i = 0; i < n_inst; ++i) {
             const int t = inst_tmpl[i];
             const int n = inst[i].n, w = n + 1;
-            for (int y0 = -1; y0 <= n - 1; y0 += 2)
-                for (int x0 = -1; x0 <= n - 1; x0 += 2) {
-                    int32_t L = 0;
-                    for (int dy = 0; dy < 2; ++dy)
-                        for (int dx = 0; dx < 2; ++dx)
-                            if (x0 + dx <= n - 1 && y0 + dy <= n - 1)
-                                L = std::max(L, padded[t][(size_t)(y0 + dy + 1) * w + (x0 + dx + 1)]);
-                    if (L > 0) li.push_back({L, CellItem{i, x0, y0, 0}});
-                }
+            const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
+            for (int py = 0; py < ph; ++py)
+                for (int px = 0; px < pw; ++px)
+                    for (int g = 0; g < G; ++g) {
+                        const int32_t V = part_len[t][((size_t)py * pw + px) * G + g];
+                        if (V > 0) li.push_back({V, CellItem{i, px * kPatchW - 1, py * kPatchH - 1, g}});
+                    }
         }
         std::stable_sort(li.begin(), li.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-        const size_t b_start = sizeof(int64_t) * start_all.size();
+        const size_t b_pbase = sizeof(int64_t) * std::max<size_t>(pbase_all.size(), 1);
+        const size_t b_cnt = sizeof(int32_t) * cnt_all.size();
         const size_t b_items = sizeof(CellItem) * std::max<size_t>(li.size(), 1);
-        const size_t b_codes = 4 * (size_t)std::max<int64_t>(entries, 1);
-        const size_t o_items_l = align(b_start), o_codes_l = align(o_items_l + b_items);
-        const size_t o_fa = align(o_codes_l + b_codes), o_fb = align(o_fa + (frac_lists ? b_codes : 0));
-        list_bytes = (int64_t)(frac_lists ? o_fb + b_codes : o_fa);
+        const size_t b_codes = 16 * (size_t)std::max<int64_t>(slots_total, 1);
+        const size_t o_cnt_l = align(b_pbase), o_items_l = align(o_cnt_l + b_cnt);
+        const size_t o_codes_l = align(o_items_l + b_items);
+        list_bytes = (int64_t)(o_codes_l + b_codes);
         if (cudaMalloc(&P.d_lists, list_bytes) != cudaSuccess) {
             P.d_lists = nullptr;
             cudaGetLastError();
@@ -933,26 +963,30 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         unsigned char* lb = static_cast<unsigned char*>(P.d_lists);
         std::vector<CellItem> items(li.size());
         for (size_t k = 0; k < li.size(); ++k) items[k] = li[k].second;
-        if (cudaMemcpyAsync(lb, start_all.data(), b_start, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        if (cudaMemcpyAsync(lb, pbase_all.data(), sizeof(int64_t) * pbase_all.size(), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(lb + o_cnt_l, cnt_all.data(), b_cnt, cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemcpyAsync(lb + o_items_l, items.data(), sizeof(CellItem) * items.size(), cudaMemcpyHostToDevice,
-                            st) != cudaSuccess)
+                            st) != cudaSuccess ||
+            cudaMemsetAsync(lb + o_codes_l, 0, b_codes, st) != cudaSuccess)
             return PAT_ERR_CUDA;
-        dp.cell_start = reinterpret_cast<const int64_t*>(lb);
+        dp.list_base = reinterpret_cast<const int64_t*>(lb);
+        dp.cell_cnt = reinterpret_cast<const int32_t*>(lb + o_cnt_l);
         dp.list_items = reinterpret_cast<const CellItem*>(lb + o_items_l);
         dp.codes = reinterpret_cast<const uint32_t*>(lb + o_codes_l);
-        dp.frac_a = frac_lists ? reinterpret_cast<const float*>(lb + o_fa) : nullptr;
-        dp.frac_b = frac_lists ? reinterpret_cast<const float*>(lb + o_fb) : nullptr;
-        for (int i = 0; i < n_inst; ++i) inst[i].list_off = tmpl_start_off[inst_tmpl[i]];
+        for (int i = 0; i < n_inst; ++i) {
+            inst[i].list_off = tmpl_cnt_off[inst_tmpl[i]];
+            inst[i].pbase_off = tmpl_pbase_off[inst_tmpl[i]];
+        }
         if (cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(InstDev) * inst.size(), cudaMemcpyHostToDevice, st) !=
             cudaSuccess)
             return PAT_ERR_CUDA;
-        // fill the lists (same enumeration, same order), padding included
+        // fill the lists (same enumeration, same order; null entries end each cell's last vector)
         for (size_t t = 0; t < tmpls.size(); ++t) {
             const int i = rep[t];
-            if (launch_adj_build(dp, i, inst[i].n, nullptr, dp.cell_start + tmpl_start_off[t],
-                                 reinterpret_cast<uint32_t*>(lb + o_codes_l),
-                                 frac_lists ? reinterpret_cast<float*>(lb + o_fa) : nullptr,
-                                 frac_lists ? reinterpret_cast<float*>(lb + o_fb) : nullptr, st) != cudaSuccess)
+            if (launch_adj_build(dp, i, inst[i].n, const_cast<int32_t*>(dp.cell_cnt) + tmpl_cnt_off[t],
+                                 dp.list_base + tmpl_pbase_off[t], reinterpret_cast<uint32_t*>(lb + o_codes_l),
+                                 frac_lists, st) != cudaSuccess)
                 return PAT_ERR_CUDA;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
@@ -962,7 +996,6 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         if (lbps < 1) return PAT_ERR_UNSUPPORTED;
         dp.cell_blocks = (int)std::max<int64_t>(
             1, std::min<int64_t>((int64_t)lbps * P.num_sms, ((int64_t)li.size() + 7) / 8));
-        dp.adj_groups = 1;
     }
 
     // ---- info -------------------------------------------------------------

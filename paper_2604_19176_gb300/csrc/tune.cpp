@@ -198,12 +198,9 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
     // ---- adjoint candidates (with the best forward shape) ------------------
     best_ms = 1e30f;
     pat_options_t fwd_opt = best_opt;
-    // list modes have no further shape; the enumeration mode splits detectors into groups
+    // the list modes cut each cell's list into groups, the enumeration mode its detectors
     std::vector<std::pair<int, int>> adj_cands;
-    if (opt.adj_mode == 2)
-        for (int gcount : {0, 1, 2, 4, 8}) adj_cands.push_back({2, gcount});
-    else
-        adj_cands.push_back({opt.adj_mode, 0});
+    for (int gcount : {0, 1, 2, 4, 8}) adj_cands.push_back({opt.adj_mode, gcount});
     for (auto& ac : adj_cands) {
         pat_options_t o = fwd_opt;
         o.adj_mode = ac.first;
