@@ -112,7 +112,7 @@ typedef struct {
                          /*   4 or 8; 0 = auto (more when there are fewer tiles than SMs)     */
     int32_t tile_cols;   /* max pixel columns of a circular-mean tile; 0 = auto               */
     int32_t time_pair;   /* time stages of pat_tv_step / pat_pdhg_step: 0 = auto (one fused   */
-                         /*   launch per step where its shared memory fits: n_t up to ~2400), */
+                         /*   launch per step where its shared memory fits: n_t up to ~4400), */
                          /*   1 = separate launches (radius sums, forward, adjoint)          */
     int32_t reserved[5];
 } pat_options_t;

@@ -234,8 +234,8 @@ cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st)
 // early adjoint chunks are the long ones).  The contraction of a chunk is
 // cut into blocks of 32 rows; warp w takes blocks w, w + 8, ... of each of
 // its CTA's chunks and walks them without CTA-wide synchronisation: a lane
-// owns one output for all 8 detectors (8 accumulators; a row's 8 detector
-// values are two broadcast 16-byte shared-memory loads), and the block's 32
+// owns one output for all kTimeJ detectors (kTimeJ accumulators; a row's
+// detector values are broadcast 16-byte shared-memory loads), and the block's 32
 // values of P for that output sit in registers, loaded one block ahead
 // (the loads of the first block are issued before the dependency wait: P
 // does not depend on the data).  After a phase the warps' partial sums are
@@ -243,6 +243,8 @@ cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st)
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kTimeThreads = kTimeWarps * kWarp;
+constexpr int kTimeSub = kTimeWarps / kTimeJ;   // warps per detector in the sums and epilogues
+static_assert(kTimeJ % 4 == 0 && kTimeWarps % kTimeJ == 0, "fused time stage shape");
 
 // chunk p of a rank (p = 0, 1, ...) and the rank that owns chunk c
 __device__ __forceinline__ int time_chunk(int p, int rank)
@@ -332,6 +334,7 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
     const TimeGroup grp = dp.time_groups[blockIdx.x / kTimeCS];
     const InstDev in = dp.inst[grp.inst];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int jd = w % kTimeJ, sub = w / kTimeJ;   // sums and epilogues: detector, and chunks p = sub (mod kTimeSub)
     const int n_tc = in.n_tp >> 5, n_rc = in.n_rp >> 5;
     const float* PT = dp.P + in.p_off + (size_t)in.n_tp * in.n_rp + lane;   // P^T: row m, pitch n_tp
     const float* PP = dp.P + in.p_off + lane;                               // P: row t, pitch n_rp
@@ -350,16 +353,14 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
         const float* ab = (it.phase == 0 ? Ms : rs) + (size_t)(32 * it.kc) * kTimeJ;
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
-            const float4 a0 = *reinterpret_cast<const float4*>(ab + r * kTimeJ);
-            const float4 a1 = *reinterpret_cast<const float4*>(ab + r * kTimeJ + 4);
-            acc[0] = fmaf(pv[r], a0.x, acc[0]);
-            acc[1] = fmaf(pv[r], a0.y, acc[1]);
-            acc[2] = fmaf(pv[r], a0.z, acc[2]);
-            acc[3] = fmaf(pv[r], a0.w, acc[3]);
-            acc[4] = fmaf(pv[r], a1.x, acc[4]);
-            acc[5] = fmaf(pv[r], a1.y, acc[5]);
-            acc[6] = fmaf(pv[r], a1.z, acc[6]);
-            acc[7] = fmaf(pv[r], a1.w, acc[7]);
+#pragma unroll
+            for (int h = 0; h < kTimeJ / 4; ++h) {
+                const float4 a = *reinterpret_cast<const float4*>(ab + r * kTimeJ + 4 * h);
+                acc[4 * h + 0] = fmaf(pv[r], a.x, acc[4 * h + 0]);
+                acc[4 * h + 1] = fmaf(pv[r], a.y, acc[4 * h + 1]);
+                acc[4 * h + 2] = fmaf(pv[r], a.z, acc[4 * h + 2]);
+                acc[4 * h + 3] = fmaf(pv[r], a.w, acc[4 * h + 3]);
+            }
         }
         if (it.last) {   // this warp's partial sums of the chunk
             float* dst = red + (size_t)((it.p * kTimeWarps + w) * kTimeJ) * kWarp + lane;
@@ -397,31 +398,31 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
     pdl_wait();   // the partial slots come from the circular-mean kernel; g and y from earlier work
 
     // the data (and y) of this CTA's time chunks, for the forward epilogue
-    for (int p = 0; time_chunk(p, rank) < n_tc; ++p) {
+    for (int p = sub; time_chunk(p, rank) < n_tc; p += kTimeSub) {
         const int x = 32 * time_chunk(p, rank) + lane;
-        const bool ok = w < grp.jn && x < in.n_t;
-        const size_t o = ok ? in.g_off + (size_t)(grp.j0 + w) * in.n_t + x : 0;
-        float* d = gs + (size_t)(p * 2 * kTimeJ + w) * kWarp + lane;
+        const bool ok = jd < grp.jn && x < in.n_t;
+        const size_t o = ok ? in.g_off + (size_t)(grp.j0 + jd) * in.n_t + x : 0;
+        float* d = gs + (size_t)(p * 2 * kTimeJ + jd) * kWarp + lane;
         cp_async4_zfill(d, gdata + o, ok);
         if (DUAL) cp_async4_zfill(d + kTimeJ * kWarp, y + o, ok);
     }
     cp_async_commit();
 
-    // 1. M of this CTA's radius chunks: thread = (detector w, radius lane of the chunk),
-    //    kU chunks at a time with 8 slots of each in flight
+    // 1. M of this CTA's radius chunks: thread = (detector jd, radius lane of the chunk)
+    //    for chunks p = sub (mod kTimeSub), kU chunks at a time with 8 slots of each in flight
     {
         constexpr int kU = 2;
-        const bool jok = w < grp.jn;
-        const int jj = grp.j0 + (jok ? w : 0);
+        const bool jok = jd < grp.jn;
+        const int jj = grp.j0 + (jok ? jd : 0);
         const size_t plane = (size_t)in.n_det * in.n_r;
         const float* src = dp.mpart + in.mpart_off + (size_t)jj * in.n_r;
         const int32_t* cnt_row = reinterpret_cast<const int32_t*>(dp.slotcnt + in.slotcnt_off) + (size_t)jj * in.nmb;
-        for (int p0 = 0; time_chunk(p0, rank) < n_rc; p0 += kU) {
+        for (int p0 = sub; time_chunk(p0, rank) < n_rc; p0 += kU * kTimeSub) {
             int m[kU], cnt[kU], cmax = 0;
             float s[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int c = time_chunk(p0 + u, rank);
+                const int c = time_chunk(p0 + u * kTimeSub, rank);
                 m[u] = 32 * c + lane;
                 cnt[u] = (c < n_rc && jok && m[u] < in.n_r) ? __ldg(cnt_row + m[u] / dp.m_lanes) : 0;
                 cmax = max(cmax, cnt[u]);
@@ -442,13 +443,14 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u)
-                if (time_chunk(p0 + u, rank) < n_rc) Ms[m[u] * kTimeJ + w] = s[u];
+                if (time_chunk(p0 + u * kTimeSub, rank) < n_rc) Ms[m[u] * kTimeJ + jd] = s[u];
         }
     }
     cluster_arrive();
     cluster_wait();   // every CTA's share of M is in place
-    for (int idx = tid; idx < n_rc * 64; idx += kTimeThreads) {   // chunk c = float4s [64 c, 64 c + 64)
-        const int own = time_owner(idx >> 6);
+    constexpr int kChunkF4 = 32 * kTimeJ / 4;   // float4s of one chunk of rows
+    for (int idx = tid; idx < n_rc * kChunkF4; idx += kTimeThreads) {
+        const int own = time_owner(idx / kChunkF4);
         if (own != rank)
             reinterpret_cast<float4*>(Ms)[idx] = reinterpret_cast<const float4*>(cluster.map_shared_rank(Ms, own))[idx];
     }
@@ -458,18 +460,18 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
     run_phase(0);
     cp_async_wait_group<0>();   // this thread's data (and y) of its outputs
     __syncthreads();            // every warp's partial sums are in place
-    for (int p = 0; time_chunk(p, rank) < n_tc; ++p) {   // thread = (detector w, output lane)
+    for (int p = sub; time_chunk(p, rank) < n_tc; p += kTimeSub) {   // thread = (detector jd, output lane)
         const int c = time_chunk(p, rank);
         int lo, hi;
         time_blocks(0, c, in.n_r, n_tc, lo, hi);
         const int nw = min(kTimeWarps, hi - lo);   // warps that had blocks of this chunk
         float sum = 0.f;
-        for (int ww = 0; ww < nw; ++ww) sum += red[(size_t)((p * kTimeWarps + ww) * kTimeJ + w) * kWarp + lane];
+        for (int ww = 0; ww < nw; ++ww) sum += red[(size_t)((p * kTimeWarps + ww) * kTimeJ + jd) * kWarp + lane];
         const int x = 32 * c + lane;
         float r = 0.f;
-        if (w < grp.jn && x < in.n_t) {
-            const float* d = gs + (size_t)(p * 2 * kTimeJ + w) * kWarp + lane;
-            const size_t o = in.g_off + (size_t)(grp.j0 + w) * in.n_t + x;
+        if (jd < grp.jn && x < in.n_t) {
+            const float* d = gs + (size_t)(p * 2 * kTimeJ + jd) * kWarp + lane;
+            const size_t o = in.g_off + (size_t)(grp.j0 + jd) * in.n_t + x;
             const float g = sum * in.inv_K;
             if (DUAL) {
                 r = fmaf(sigma, g - d[0], d[kTimeJ * kWarp]) * inv1ps;
@@ -479,14 +481,14 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
                 if (y) y[o] = r;
             }
         }
-        rs[x * kTimeJ + w] = r;   // zero for absent detectors and padded times
+        rs[x * kTimeJ + jd] = r;   // zero for absent detectors and padded times
     }
 
     // 3. exchange of the residual chunks
     cluster_arrive();
     cluster_wait();   // every CTA's residual chunks are in place
-    for (int idx = tid; idx < n_tc * 64; idx += kTimeThreads) {
-        const int own = time_owner(idx >> 6);
+    for (int idx = tid; idx < n_tc * kChunkF4; idx += kTimeThreads) {
+        const int own = time_owner(idx / kChunkF4);
         if (own != rank)
             reinterpret_cast<float4*>(rs)[idx] = reinterpret_cast<const float4*>(cluster.map_shared_rank(rs, own))[idx];
     }
@@ -496,15 +498,15 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
     // 4. adjoint blocks, then the CTA's radius chunks of Mbar
     run_phase(1);
     __syncthreads();
-    for (int p = 0; time_chunk(p, rank) < n_rc; ++p) {
+    for (int p = sub; time_chunk(p, rank) < n_rc; p += kTimeSub) {
         const int c = time_chunk(p, rank);
         int lo, hi;
         time_blocks(1, c, in.n_r, n_tc, lo, hi);
         const int nw = min(kTimeWarps, hi - lo);
         float sum = 0.f;
-        for (int ww = 0; ww < nw; ++ww) sum += red[(size_t)((p * kTimeWarps + ww) * kTimeJ + w) * kWarp + lane];
+        for (int ww = 0; ww < nw; ++ww) sum += red[(size_t)((p * kTimeWarps + ww) * kTimeJ + jd) * kWarp + lane];
         const int x = 32 * c + lane;
-        if (w < grp.jn && x < in.n_r) dp.mbar[in.mbar_off + (size_t)(grp.j0 + w) * in.m_pitch + x] = sum;
+        if (jd < grp.jn && x < in.n_r) dp.mbar[in.mbar_off + (size_t)(grp.j0 + jd) * in.m_pitch + x] = sum;
     }
     cluster_wait();   // no CTA leaves while another may still read its shared memory
 }

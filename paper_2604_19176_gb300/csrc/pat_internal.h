@@ -101,9 +101,9 @@ struct TimeTile {
 struct TimeGroup {
     int32_t inst, j0, jn, pad;
 };
-constexpr int kTimeJ = 8;          // detectors per fused time group
+constexpr int kTimeJ = 4;          // detectors per fused time group
 constexpr int kTimeCS = 8;         // CTAs per cluster of the fused time stage
-constexpr int kTimeWarps = 8;      // warps per fused time CTA (one detector each in the epilogues)
+constexpr int kTimeWarps = 8;      // warps per fused time CTA
 
 // Adjoint cell item of instance inst: the 8 x 4 patch of cells with
 // lower-left cell (x0, y0) (absolute indices, >= -1); in enumeration mode for

@@ -2,15 +2,15 @@
 
 One launch per step replaces the radius sums of the circular means, the
 forward Abel stage with the residual (or the dual update), and the adjoint
-Abel stage; a thread-block cluster owns 8 detectors' rows.  Checked here:
+Abel stage; a thread-block cluster owns 4 detectors' rows.  Checked here:
   - the TV step through the fused stage against the FP64 oracle of
     f - tau (A^T (A f - g) + lam grad TV_eps(f)), relative to the update;
   - the primal-dual step's dual variable y = sigma (A fbar - g) / (1 + sigma)
     from y = 0 against the oracle's A;
   - fused and separate plans (time_pair = 0 / 1) agree to FP32 summation
     order, on detector counts that leave a partial group, time axes shorter
-    than one chunk per cluster CTA, a 2048-sample time axis (one CTA per SM),
-    and an uneven batch;
+    than one chunk per cluster CTA, a 2048-sample time axis, and an uneven
+    batch;
   - a time axis too long for the fused stage's shared memory falls back to the
     separate launches (plan info time_pair = 0).
 """
@@ -128,11 +128,11 @@ def test_fused_stage_is_deterministic(cuda_dev):
 
 
 def test_long_time_axis_falls_back_to_separate_launches(cuda_dev):
-    g = Geometry(32, 6, 0.0, math.pi, 3000, 2.0, 32)
+    g = Geometry(32, 6, 0.0, math.pi, 6000, 2.0, 32)
     plan = PatPlan(g, device=cuda_dev)
     assert plan.info()["time_pair"] == 0
     f_np = f32(np.abs(inputs.random_image(32, seed=78)))
-    d_np = f32(inputs.random_data(6, 3000, seed=79))
+    d_np = f32(inputs.random_data(6, 6000, seed=79))
     out = torch.empty(32, 32, device=cuda_dev)
     plan.tv_step(torch.tensor(f_np, dtype=torch.float32, device=cuda_dev), out,
                  torch.tensor(d_np, dtype=torch.float32, device=cuda_dev), 0.5, 0.0, 1e-2, nonneg=False)
