@@ -43,7 +43,10 @@ std::string tune_key(const pat_geometry_t* geoms, int n, const pat_options_t& op
         put(&g.t_max, sizeof g.t_max);
         put(&g.n_angles, sizeof g.n_angles);
     }
+    // the requested fields the tuner keeps (it searches the tile shapes and groups)
     put(&opt.image_dtype, sizeof opt.image_dtype);
+    put(&opt.adj_mode, sizeof opt.adj_mode);
+    put(&opt.time_pair, sizeof opt.time_pair);
     put(&device, sizeof device);
     return k;
 }
