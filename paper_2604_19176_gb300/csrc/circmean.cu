@@ -100,15 +100,22 @@ __device__ __forceinline__ UnitFrame unit_frame(const Segment& sg, const InstDev
 }
 
 // One sample (radius mf, ray r = (hi_u, hi_v, lo_u, lo_v)) of the staged tile.
-__device__ __forceinline__ float sample(const unsigned char* __restrict__ smem, const UnitFrame& u, float mf,
-                                        float4 r, float Uf, float Vf)
+// The u and v halves of the split form run as f32x2 pairs (m2 = (mf, mf),
+// f0 = (Uf, Vf)), in the order of cell_rel and cell_frac: t = floor_biased of
+// fma(m, hi, f0); -cell = kMagic - t (exact); a = fma(m, hi, -cell) +
+// fma(m, lo, f0).
+__device__ __forceinline__ float sample(const unsigned char* __restrict__ smem, const UnitFrame& u,
+                                        unsigned long long m2, float4 r, unsigned long long f0)
 {
-    const float tu = floor_biased(__fmaf_rn(mf, r.x, Uf));
-    const float tv = floor_biased(__fmaf_rn(mf, r.y, Vf));
-    const float fu = __fsub_rn(tu, kMagic), fv = __fsub_rn(tv, kMagic);
-    const float a = cell_frac(mf, r.x, r.z, Uf, fu), b = cell_frac(mf, r.y, r.w, Vf, fv);
-    const uint32_t iu = min(max(__float_as_uint(tu), u.ulo), u.uhi);
-    const uint32_t iv = min(max(__float_as_uint(tv), u.vlo), u.vhi);
+    const unsigned long long hi = f2_pack(r.x, r.y), lo = f2_pack(r.z, r.w);
+    const unsigned long long magic2 = f2_pack(kMagic, kMagic);
+    const unsigned long long t = f2_add_rd(f2_fma(m2, hi, f0), magic2);   // biased floors (tu, tv)
+    const unsigned long long ncell = f2_sub(magic2, t);                   // (-cell_u, -cell_v)
+    const float2 ab = f2_unpack(f2_add(f2_fma(m2, hi, ncell), f2_fma(m2, lo, f0)));
+    const float2 tt = f2_unpack(t);
+    const float a = ab.x, b = ab.y;
+    const uint32_t iu = min(max(__float_as_uint(tt.x), u.ulo), u.uhi);
+    const uint32_t iv = min(max(__float_as_uint(tt.y), u.vlo), u.vhi);
     const float4 c = *reinterpret_cast<const float4*>(smem + (iv * u.row_bytes + iu * 16u + u.koff));
     return fmaf(b, fmaf(a, c.w, c.z), fmaf(a, c.y, c.x));
 }
@@ -176,16 +183,17 @@ __global__ void __launch_bounds__(kCircThreads, 2) k_circmean(DevPlan dp, const 
             const float4 d = __ldg(det + un.j);
             const UnitFrame fr = unit_frame(sg, in, d);
             const float4* tq = rays_s + un.q0 + ql;   // units never wrap past K
+            const unsigned long long m2 = f2_pack(mf, mf), f0 = f2_pack(d.z, d.w);
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
             int i = ql;
             for (; i + 3 * QL < un.nq; i += 4 * QL, tq += 4 * QL) {
                 const float4 c0 = tq[0], c1 = tq[QL], c2 = tq[2 * QL], c3 = tq[3 * QL];
-                acc0 += sample(smem_raw, fr, mf, c0, d.z, d.w);
-                acc1 += sample(smem_raw, fr, mf, c1, d.z, d.w);
-                acc2 += sample(smem_raw, fr, mf, c2, d.z, d.w);
-                acc3 += sample(smem_raw, fr, mf, c3, d.z, d.w);
+                acc0 += sample(smem_raw, fr, m2, c0, f0);
+                acc1 += sample(smem_raw, fr, m2, c1, f0);
+                acc2 += sample(smem_raw, fr, m2, c2, f0);
+                acc3 += sample(smem_raw, fr, m2, c3, f0);
             }
-            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(smem_raw, fr, mf, *tq, d.z, d.w);
+            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(smem_raw, fr, m2, *tq, f0);
             float acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
             for (int o = ML; o < kWarp; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

@@ -40,6 +40,49 @@ constexpr uint32_t kMagicBits = 0x4B400000u;
 __device__ __forceinline__ float floor_biased(float x) { return __fadd_rd(x, kMagic); }
 
 // ---------------------------------------------------------------------------
+// Paired FP32 arithmetic (Blackwell f32x2): two independent FP32 operations in
+// one instruction on a 64-bit register pair; each half is rounded exactly as
+// the scalar operation with the same rounding mode, so a paired evaluation of
+// the u and v halves of the split form gives the bits of cell_rel/cell_frac.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_add_rd(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
 // Programmatic dependent launch.  Kernels of the operator chain are launched
 // with programmatic stream serialization, so the next kernel is launched as
 // soon as this one's CTAs exit (its launch overlaps the end of this one);
