@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
                 }
             }
         } else {
-            const float cxf = (float)(cx - in.c0), cyf = (float)(cy - in.c0);
+            const unsigned long long cxy = f2_pack((float)(cx - in.c0), (float)(cy - in.c0));
             const float4* det = dp.det + in.det_off;
             const float4* rays = dp.rays + in.ray_off;
             const int mbits = in.code_mbits, qshift = in.code_jbits + in.code_mbits;
@@ -292,9 +292,14 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
                 const float wv = __ldg(mb + widx);
                 const float4 d = __ldg(det + j);
                 const float4 r = __ldg(rays + q);
-                // the sample lies in this cell: its relative cell is (cxf, cyf) - floor(U, V)
-                const float cxr = __fsub_rn(cxf, d.x), cyr = __fsub_rn(cyf, d.y);
-                acc.add(wv, cell_frac(mf, r.x, r.z, d.z, cxr), cell_frac(mf, r.y, r.w, d.w, cyr));
+                // the sample lies in this cell: its relative cell is (cxf, cyf) - floor(U, V), so
+                // -cell = floor(U, V) - (cxf, cyf) (exact), and (a, b) is cell_frac's sequence in
+                // f32x2 pairs: fma(m, hi, -cell) + fma(m, lo, f0)
+                const unsigned long long m2 = f2_pack(mf, mf);
+                const unsigned long long ncell = f2_sub(f2_pack(d.x, d.y), cxy);
+                const float2 ab = f2_unpack(f2_add(f2_fma(m2, f2_pack(r.x, r.y), ncell),
+                                                   f2_fma(m2, f2_pack(r.z, r.w), f2_pack(d.z, d.w))));
+                acc.add(wv, ab.x, ab.y);
             };
             // four vectors in flight per lane, then their 16 entries
             for (int kb = 0; kb < nk; kb += 4) {
