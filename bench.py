@@ -55,7 +55,7 @@ def parse(argv=None):
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--profile", action="store_true", help="short run for ncu captures (no flush, no extras)")
     p.add_argument("--tile", default="",
-                   help="fixed tile shape m_lanes,q_piece,band_rows,adj_groups,adj_mode,abel_split[,tile_cols] "
+                   help="fixed tile shape m_lanes,q_piece,band_rows,adj_groups,adj_mode,abel_split[,tile_cols[,adj_jblock]] "
                         "instead of the autotuner (e.g. the tile_shape a previous run reported), for reproducible "
                         "profiles")
     return p.parse_args(argv)
@@ -623,8 +623,9 @@ def main():
         vals = [int(x) for x in args.tile.split(",")]
         ml, qp, br, ag, am, sp = vals[:6]
         tc = vals[6] if len(vals) > 6 else 0
+        st_ = vals[7] if len(vals) > 7 else 0
         plan = PatPlan(g, device=dev, m_lanes=ml, q_piece=qp, band_rows=br, adj_groups=ag, adj_mode=am,
-                       abel_split=sp, tile_cols=tc)
+                       abel_split=sp, tile_cols=tc, adj_jblock=st_)
     else:
         plan = PatPlan(g, device=dev, tune=1)  # autotuned tile shapes (timed at plan creation)
     info = plan.info()
@@ -796,7 +797,8 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * n_steps,
                 "tile_shape": {k: info[k] for k in ("m_lanes", "q_piece", "band_rows", "tile_cols", "bands_max",
-                                                    "adj_groups", "adj_mode", "abel_split_fwd", "abel_split_adj")},
+                                                    "adj_groups", "adj_mode", "abel_split_fwd", "abel_split_adj",
+                                                    "adj_jblock")},
                 "samples_per_application": samples, "sample_slots": info["sample_slots"],
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
                 "extras": extras}

@@ -103,18 +103,25 @@ typedef struct {
     int32_t q_piece;     /* max angular nodes per work unit (multiple of 4); 0 = auto        */
     int32_t band_rows;   /* max pixel rows of a circular-mean tile; 0 = auto                 */
     int32_t adj_groups;  /* detector groups of the adjoint gather, 1..16; 0 = auto           */
-    int32_t adj_mode;    /* adjoint gather: 0 = auto (1 if it fits the list budget, else 3,   */
-                         /*   else 2), 1 = per-cell sample code lists built at creation       */
-                         /*   (device memory ~4 B per sample), 2 = enumerate on every call    */
-                         /*   (no list memory), 3 = per-cell fraction lists built at creation */
-                         /*   (~12 B per sample: Mbar index and the FP32 bilinear fractions)  */
+    int32_t adj_mode;    /* adjoint gather: 0 = auto (4 if it fits the list budget, else 1,   */
+                         /*   else 3, else 2); 1 = per-cell sample code lists built at        */
+                         /*   creation (device memory ~4 B per sample); 2 = enumerate on      */
+                         /*   every call (no list memory); 3 = per-cell fraction lists built  */
+                         /*   at creation (~12 B per sample: Mbar index and the FP32 bilinear */
+                         /*   fractions); 4 = per-cell run-pair code lists (one 4 B code per  */
+                         /*   pair of samples at consecutive radii of one ray, or per lone    */
+                         /*   sample; needs one code bit more than 1)                         */
     int32_t abel_split;  /* CTAs (a thread-block cluster) sharing each time-stage tile: 1, 2, */
                          /*   4 or 8; 0 = auto (more when there are fewer tiles than SMs)     */
     int32_t tile_cols;   /* max pixel columns of a circular-mean tile; 0 = auto               */
     int32_t time_pair;   /* time stages of pat_tv_step / pat_pdhg_step: 0 = auto (one fused   */
                          /*   launch per step where its shared memory fits: n_t up to ~4400), */
                          /*   1 = separate launches (radius sums, forward, adjoint)          */
-    int32_t reserved[5];
+    int32_t adj_jblock;  /* code lists (adj_mode 1, 4): detectors per aligned block, 1..16384; */
+                         /*   the 32 cells of a patch enter each block together (shorter      */
+                         /*   lists wait on null entries) so that a warp's table loads share  */
+                         /*   cache lines; 0 = auto                                           */
+    int32_t reserved[4];
 } pat_options_t;
 
 /* Plan statistics (pat_plan_info). */
@@ -131,12 +138,14 @@ typedef struct {
     int32_t m_lanes, q_piece, band_rows, adj_groups; /* tile shape in use              */
     int32_t bands_max;       /* largest number of circular-mean tiles of any instance     */
     int32_t adj_mode;        /* adjoint gather in use: 1 = code lists, 2 = enumeration,   */
-                             /*   3 = fraction lists                                      */
+                             /*   3 = fraction lists, 4 = run-pair code lists             */
     int64_t list_bytes;      /* device memory of the adjoint sample lists                 */
     int32_t abel_split_fwd;  /* CTAs per forward / adjoint time-stage tile in use         */
     int32_t abel_split_adj;
     int32_t tile_cols;       /* widest circular-mean tile (pixels); band_rows the tallest */
     int32_t time_pair;       /* 1 = the steps run the fused time stage, 0 = separate      */
+    int32_t adj_jblock;      /* detectors per aligned block of the code lists (0: none)   */
+    int32_t reserved;
 } pat_plan_info_t;
 
 /*

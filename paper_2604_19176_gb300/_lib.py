@@ -42,7 +42,8 @@ class PatOptions(ctypes.Structure):
         ("image_dtype", ctypes.c_int32), ("schedule", ctypes.c_int32), ("tune", ctypes.c_int32),
         ("m_lanes", ctypes.c_int32), ("q_piece", ctypes.c_int32), ("band_rows", ctypes.c_int32),
         ("adj_groups", ctypes.c_int32), ("adj_mode", ctypes.c_int32), ("abel_split", ctypes.c_int32),
-        ("tile_cols", ctypes.c_int32), ("time_pair", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+        ("tile_cols", ctypes.c_int32), ("time_pair", ctypes.c_int32), ("adj_jblock", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -54,7 +55,8 @@ class PatPlanInfo(ctypes.Structure):
         ("m_lanes", ctypes.c_int32), ("q_piece", ctypes.c_int32), ("band_rows", ctypes.c_int32),
         ("adj_groups", ctypes.c_int32), ("bands_max", ctypes.c_int32), ("adj_mode", ctypes.c_int32),
         ("list_bytes", ctypes.c_int64), ("abel_split_fwd", ctypes.c_int32), ("abel_split_adj", ctypes.c_int32),
-        ("tile_cols", ctypes.c_int32), ("time_pair", ctypes.c_int32),
+        ("tile_cols", ctypes.c_int32), ("time_pair", ctypes.c_int32), ("adj_jblock", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

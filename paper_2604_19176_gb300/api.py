@@ -58,7 +58,7 @@ class PatPlan:
     def __init__(self, geoms: Geometry | Sequence[Geometry], *, image_dtype=torch.float32, device=None,
                  m_lanes: int = 0, q_piece: int = 0, band_rows: int = 0, adj_groups: int = 0,
                  adj_mode: int = 0, abel_split: int = 0, tile_cols: int = 0, time_pair: int = 0, schedule: int = 0,
-                 tune: int = 0, stream=None):
+                 tune: int = 0, adj_jblock: int = 0, stream=None):
         self._lib = _lib.load()
         if isinstance(geoms, Geometry):
             geoms = [geoms]
@@ -79,6 +79,7 @@ class PatPlan:
         opt.abel_split = abel_split
         opt.tile_cols = tile_cols
         opt.time_pair = time_pair
+        opt.adj_jblock = adj_jblock
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = _stream_ptr(stream, self.device)

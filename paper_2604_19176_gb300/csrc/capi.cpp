@@ -159,7 +159,8 @@ pat_status_t pat_plan_create(const pat_geometry_t* geoms, int32_t n_instances, c
     if (opt.tile_cols != 0 && (opt.tile_cols < 1 || opt.tile_cols > 8192)) return PAT_ERR_INVALID_ARG;
     if (opt.adj_groups < 0 || opt.adj_groups > 16) return PAT_ERR_INVALID_ARG;
     if (opt.time_pair != 0 && opt.time_pair != 1) return PAT_ERR_INVALID_ARG;
-    if (opt.adj_mode < 0 || opt.adj_mode > 3) return PAT_ERR_INVALID_ARG;
+    if (opt.adj_mode < 0 || opt.adj_mode > 4) return PAT_ERR_INVALID_ARG;
+    if (opt.adj_jblock < 0 || opt.adj_jblock > 16384) return PAT_ERR_INVALID_ARG;
     if (opt.abel_split != 0 && opt.abel_split != 1 && opt.abel_split != 2 && opt.abel_split != 4 &&
         opt.abel_split != 8)
         return PAT_ERR_INVALID_ARG;

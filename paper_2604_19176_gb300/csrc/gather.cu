@@ -15,17 +15,23 @@
 // the forward's split-form expression.  Hits come out in the order (j, q, m).
 //
 // Three ways to run this:
-//   code lists (the default when 4 B per sample fits the list budget and a
-//     (q, j, m) code fits 32 bits): at plan creation the enumeration runs
-//     twice (count, then fill) to store every cell's hits as packed codes,
-//     the 32 cells of an 8 x 4 patch interleaved vector by vector so that a
-//     warp streams them with full 512-byte loads; each call recomputes a and b
-//     from the codes with the forward's expressions (k_adj_list).
+//   code lists (when 4 B per sample fits the list budget and a (q, j, m)
+//     code fits 32 bits): at plan creation the enumeration runs twice
+//     (count, then fill) to store every cell's hits as packed codes, the 32
+//     cells of an 8 x 4 patch interleaved vector by vector so that a warp
+//     streams them with full 512-byte loads; each call recomputes a and b
+//     from the codes with the forward's expressions (k_adj_list).  The
+//     default form is run pairs: most hits of a cell come in runs of two
+//     consecutive radii on one ray (a cell is about two radius steps wide),
+//     and one code then stands for both, so the pair shares its detector and
+//     ray loads and the code stream shrinks by about 40 %.
 //   fraction lists (12 B per sample): the hits as (Mbar index, a, b), a and b
 //     the exact FP32 values the forward computes (one table load per sample,
 //     no coordinate arithmetic, but a 3x larger stream).
 //   compute mode: the enumeration runs on every call (k_adj_cells), one warp
 //     per 8 x 4 patch of cells and detector group, partial Z per group.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -145,12 +151,22 @@ __global__ void __launch_bounds__(256, 5) k_adj_cells(DevPlan dp)
 }
 
 // ---------------------------------------------------------------------------
-// List building (plan creation): count (MODE 0), then fill, the hits of every
-// cell of instance `inst_idx`, all detectors, in enumeration order.  Thread =
-// cell.  MODE 1: packed codes q << (jb + mb) | j << mb | m; MODE 2: the Mbar
-// index j * m_pitch + m and the fractions a, b.  Entry k of a cell goes to
-// vector k / 4 of the part that holds that vector, component k % 4, then
-// null entries fill the last vector (layout in pat_internal.h).
+// List building (plan creation), thread = cell, hits in enumeration order
+// (j, q, m) over all detectors of instance `inst_idx` (layouts in
+// pat_internal.h).
+//
+// Fraction lists: k_adj_build<0> counts every cell's samples, then
+// k_adj_build<2> stores sample k of a cell (Mbar index j * m_pitch + m and
+// the fractions a, b) in vector k / 4 of the part holding that vector,
+// component k % 4, and null entries fill the cell's last vector.
+//
+// Code lists: k_adj_seg<PAIRS, false> takes, for every (patch, detector
+// block), the longest entry count of the patch's cells (atomicMax into
+// segmax); the host turns those into segment starts; k_adj_seg<PAIRS, true>
+// then writes entry i of block b of a cell at position seg[b] + i of the
+// patch's sequence, over a buffer that holds null codes everywhere else.
+// PAIRS: two hits of one (j, q) at radii m, m + 1 make one entry, coded at m
+// with bit 31 set.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int32_t* __restrict__ counts,
@@ -162,9 +178,8 @@ __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int
     if (idx >= w * w) return;
     const int cxa = idx % w, cya = idx / w;   // cell index + 1
     const float cxf = (float)(cxa - 1 - in.c0), cyf = (float)(cya - 1 - in.c0);
-    const int mb = in.code_mbits, jmb = in.code_jbits + in.code_mbits;
+    const int mb = in.code_mbits;
     const int G = dp.adj_groups;
-    constexpr int S = MODE == 2 ? 3 : 1;   // 16-byte slots per vector
     int count = 0, nv = 0, lane = 0;
     const int64_t* pb = nullptr;
     if (MODE) {
@@ -173,29 +188,22 @@ __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int
         pb = pbase + ((int64_t)(cya / kPatchH) * in.patches_x + cxa / kPatchW) * G;
         lane = (cya % kPatchH) * kPatchW + cxa % kPatchW;
     }
-    // part g holds vectors [v0, v1) = [g nv / G, (g + 1) nv / G); entries come in order
-    int g = 0, v0 = 0, v1 = MODE ? nv / G : 0;
-    auto put = [&](int k, uint32_t code, float a, float b) {
+    // part g holds vectors [g nv / G, (g + 1) nv / G): vector v is in part
+    // ceil((v + 1) G / nv) - 1
+    auto put = [&](int k, uint32_t widx, float a, float b) {
         const int v = k >> 2;
-        while (v >= v1) {
-            ++g;
-            v0 = v1;
-            v1 = (int)((int64_t)(g + 1) * nv / G);
-        }
-        const int64_t slot = pb[g] + (int64_t)(v - v0) * S * kWarp + lane;
+        const int g = (int)(((int64_t)(v + 1) * G + nv - 1) / nv) - 1;
+        const int v0 = (int)((int64_t)g * nv / G);
+        const int64_t slot = pb[g] + (int64_t)(v - v0) * 3 * kWarp + lane;
         const int c = k & 3;
-        out[slot * 4 + c] = code;
-        if (MODE == 2) {
-            out[(slot + kWarp) * 4 + c] = __float_as_uint(a);
-            out[(slot + 2 * kWarp) * 4 + c] = __float_as_uint(b);
-        }
+        out[slot * 4 + c] = widx;
+        out[(slot + kWarp) * 4 + c] = __float_as_uint(a);
+        out[(slot + 2 * kWarp) * 4 + c] = __float_as_uint(b);
     };
     int k = 0;
-    enumerate_cell(dp, in, cxf, cyf, 0, 1, [&](int j, int m, int q, float a, float b) {
-        if (MODE && k < count) {   // (the fill sees exactly the counted hits; never write past them)
-            const uint32_t widx = ((uint32_t)j << mb) | (uint32_t)m;
-            put(k, MODE == 1 ? (((uint32_t)q << jmb) | widx) : widx, a, b);
-        }
+    enumerate_cell(dp, in, cxf, cyf, 0, 1, [&](int j, int m, int, float a, float b) {
+        // (the fill sees exactly the counted hits; never write past them)
+        if (MODE && k < count) put(k, ((uint32_t)j << mb) | (uint32_t)m, a, b);
         ++k;
     });
     if (!MODE) {
@@ -206,16 +214,88 @@ __global__ void __launch_bounds__(256) k_adj_build(DevPlan dp, int inst_idx, int
     for (int kk = count; kk < 4 * nv; ++kk) put(kk, null_widx, 0.f, 0.f);
 }
 
+// seg: per patch, the segment start of each detector block, then the
+// patch's length in vectors (nblk + 1 entries per patch).
+template <bool PAIRS, bool FILL>
+__global__ void __launch_bounds__(256) k_adj_seg(DevPlan dp, int inst_idx, int jblock, int nblk,
+                                                 int32_t* __restrict__ seg, const int64_t* __restrict__ pbase,
+                                                 uint32_t* __restrict__ out)
+{
+    const InstDev in = dp.inst[inst_idx];
+    const int n = in.n, w = n + 1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= w * w) return;
+    const int cxa = idx % w, cya = idx / w;   // cell index + 1
+    const float cxf = (float)(cxa - 1 - in.c0), cyf = (float)(cya - 1 - in.c0);
+    const int mb = in.code_mbits, jmb = in.code_jbits + in.code_mbits;
+    const int G = dp.adj_groups;
+    const int64_t patch = (int64_t)(cya / kPatchH) * in.patches_x + cxa / kPatchW;
+    int32_t* sp = seg + patch * (nblk + 1);
+    const int lane = (cya % kPatchH) * kPatchW + cxa % kPatchW;
+    const int nv = FILL ? sp[nblk] : 0;
+    const int64_t* pb = FILL ? pbase + patch * G : nullptr;
+    int cur_b = -1, i = 0;   // current detector block, entries of this cell in it so far
+    auto emit = [&](int j, int m, int q, uint32_t flag) {
+        const int b = j / jblock;
+        if (b != cur_b) {
+            if (!FILL && cur_b >= 0) atomicMax(sp + cur_b, i);
+            cur_b = b;
+            i = 0;
+        }
+        if (FILL) {
+            const int pos = sp[b] + i;
+            const int v = pos >> 2;
+            if (v < nv) {   // (always: the fill sees exactly the counted entries)
+                const int g = (int)(((int64_t)(v + 1) * G + nv - 1) / nv) - 1;
+                const int v0 = (int)((int64_t)g * nv / G);
+                const int64_t slot = pb[g] + (int64_t)(v - v0) * kWarp + lane;
+                out[slot * 4 + (pos & 3)] =
+                    flag | ((uint32_t)q << jmb) | ((uint32_t)j << mb) | (uint32_t)m;
+            }
+        }
+        ++i;
+    };
+    int pj = -1, pq = 0, pm = 0;   // pending hit that may start a run pair
+    enumerate_cell(dp, in, cxf, cyf, 0, 1, [&](int j, int m, int q, float, float) {
+        if constexpr (PAIRS) {
+            if (pj == j && pq == q && pm + 1 == m) {
+                emit(pj, pm, pq, 0x80000000u);
+                pj = -1;
+            } else {
+                if (pj >= 0) emit(pj, pm, pq, 0u);
+                pj = j;
+                pq = q;
+                pm = m;
+            }
+        } else {
+            emit(j, m, q, 0u);
+        }
+    });
+    if (PAIRS && pj >= 0) emit(pj, pm, pq, 0u);
+    if (!FILL && cur_b >= 0) atomicMax(sp + cur_b, i);
+}
+
+__global__ void k_fill_u32(uint32_t* __restrict__ p, int64_t n, uint32_t v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
 // ---------------------------------------------------------------------------
 // List mode: lane = cell of an 8 x 4 patch, warp = (patch, part) item.  Each
 // lane streams its cell's part as 16-byte vectors (a warp's load is 512
 // contiguous bytes: the 32 cells' vectors are interleaved), four vectors in
 // flight, and accumulates the moments sum w, sum w a, sum w b, sum w a b of
-// its entries (w = Mbar[j][m]; a and b recomputed from the code exactly as
+// its samples (w = Mbar[j][m]; a and b recomputed from the code exactly as
 // the forward computes them, or stored); null entries have w = 0.  The
 // cell's four corner sums
 //     Z00 = sum w (1-a)(1-b), Z10 = sum w a (1-b), Z01 = sum w (1-a) b, Z11 = sum w a b
 // go to plane `part` of Z, each written once (no atomics, deterministic).
+// LM 0: code lists; LM 1: fraction lists; LM 2: run-pair code lists (a code
+// with bit 31 set also stands for radius m + 1 on the same ray: one
+// detector and one ray load serve both samples).  The code lists are
+// aligned by detector blocks, so all lanes of an item have the same number
+// of vectors and, at any step, read the tables of a few detectors only.
 // ---------------------------------------------------------------------------
 namespace {
 struct Moments {
@@ -231,31 +311,42 @@ struct Moments {
 };
 } // namespace
 
-template <bool FRAC>
-__global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
+// prefetch of one 16-byte vector's line into L1
+__device__ __forceinline__ void prefetch_l1(const void* p)
 {
-    pdl_wait();   // Mbar comes from the previous kernel; the queue from earlier calls
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <int LM>
+__global__ void __launch_bounds__(256, 4) k_adj_list(DevPlan dp)
+{
+    pdl_wait();   // Mbar comes from the previous kernel
     const int lane = threadIdx.x & 31;
-    int32_t* ctr = dp.work_counters + kQueueStride;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int ib = dp.warp_items[warp], ie = dp.warp_items[warp + 1];
+    constexpr int S = LM == 1 ? 3 : 1;   // 16-byte slots per vector
+    const uint4* codes = reinterpret_cast<const uint4*>(dp.codes);
     const int G = dp.adj_groups;
-    for (;;) {
-        const int item = take_item(ctr, lane);
-        if (item >= dp.n_list_items) break;
-        const CellItem it = dp.list_items[item];
+    for (int ii = ib; ii < ie; ++ii) {
+        const ListItem it = dp.list_items[ii];
+        if (ii + 1 < ie) {
+            // the next item's first vectors, on their way while this item runs
+            const ListItem nx = dp.list_items[ii + 1];
+            const uint4* Ln = codes + nx.base + lane;
+            const int np = min(nx.nk, 4) * S;
+            for (int u = 0; u < np; ++u) prefetch_l1(Ln + (size_t)u * kWarp);
+        }
         const InstDev in = dp.inst[it.inst];
         const int n = in.n, w = n + 1;
         const int cx = it.x0 + (lane & (kPatchW - 1)), cy = it.y0 + lane / kPatchW;
         if (cx > n - 1 || cy > n - 1) continue;
         const int cell = (cy + 1) * w + (cx + 1);
-        const int nv = (dp.cell_cnt[in.list_off + cell] + 3) >> 2;
-        const int v0 = (int)((int64_t)it.group * nv / G);
-        const int nk = (int)((int64_t)(it.group + 1) * nv / G) - v0;
-        const int64_t pbi =
-            in.pbase_off + ((int64_t)((it.y0 + 1) / kPatchH) * in.patches_x + (it.x0 + 1) / kPatchW) * G + it.group;
-        const uint4* L = reinterpret_cast<const uint4*>(dp.codes) + dp.list_base[pbi] + lane;
+        const uint4* L = codes + it.base + lane;
         const float* mb = dp.mbar + in.mbar_off;
         Moments acc;
-        if constexpr (FRAC) {
+        if constexpr (LM == 1) {
+            const int nv = (dp.cell_cnt[in.list_off + cell] + 3) >> 2;
+            const int nk = (int)((int64_t)(it.group + 1) * nv / G) - (int)((int64_t)it.group * nv / G);
             // two vectors (8 entries) in flight per lane
             for (int kb = 0; kb < nk; kb += 2) {
                 uint4 ci[2], ca[2], cb[2];
@@ -280,6 +371,8 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
                 }
             }
         } else {
+            // aligned lists: every lane of the item has the block's length
+            const int nk = it.nk;
             const unsigned long long cxy = f2_pack((float)(cx - in.c0), (float)(cy - in.c0));
             const float4* det = dp.det + in.det_off;
             const float4* rays = dp.rays + in.ray_off;
@@ -287,7 +380,8 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
             const uint32_t wmask = (1u << qshift) - 1u, mmask = (1u << mbits) - 1u;
             auto entry = [&](uint32_t c) {
                 const uint32_t widx = c & wmask;
-                const int q = (int)(c >> qshift), j = (int)(widx >> mbits);
+                // (bit 31 is the pair flag in run-pair codes, the top bit of q in one-sample codes)
+                const int q = (int)((LM == 2 ? c & 0x7fffffffu : c) >> qshift), j = (int)(widx >> mbits);
                 const float mf = __uint_as_float((c & mmask) | kMagicBits) - kMagic;   // m < 2^22
                 const float wv = __ldg(mb + widx);
                 const float4 d = __ldg(det + j);
@@ -296,17 +390,28 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
                 // -cell = floor(U, V) - (cxf, cyf) (exact), and (a, b) is cell_frac's sequence in
                 // f32x2 pairs: fma(m, hi, -cell) + fma(m, lo, f0)
                 const unsigned long long m2 = f2_pack(mf, mf);
+                const unsigned long long hi = f2_pack(r.x, r.y), lo = f2_pack(r.z, r.w), f0 = f2_pack(d.z, d.w);
                 const unsigned long long ncell = f2_sub(f2_pack(d.x, d.y), cxy);
-                const float2 ab = f2_unpack(f2_add(f2_fma(m2, f2_pack(r.x, r.y), ncell),
-                                                   f2_fma(m2, f2_pack(r.z, r.w), f2_pack(d.z, d.w))));
+                const float2 ab = f2_unpack(f2_add(f2_fma(m2, hi, ncell), f2_fma(m2, lo, f0)));
                 acc.add(wv, ab.x, ab.y);
+                if constexpr (LM == 2) {
+                    // the pair's second sample, radius m + 1 (exact in FP32) on the same ray
+                    const float w2 = (int32_t)c < 0 ? __ldg(mb + widx + 1) : 0.f;
+                    const float mf2 = mf + 1.f;
+                    const unsigned long long m2b = f2_pack(mf2, mf2);
+                    const float2 ab2 = f2_unpack(f2_add(f2_fma(m2b, hi, ncell), f2_fma(m2b, lo, f0)));
+                    acc.add(w2, ab2.x, ab2.y);
+                }
             };
-            // four vectors in flight per lane, then their 16 entries
+            // four vectors in flight per lane (the next four prefetched), then their 16 entries
             for (int kb = 0; kb < nk; kb += 4) {
                 uint4 c[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     c[u] = (kb + u < nk) ? __ldcs(L + (size_t)(kb + u) * kWarp) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int u = 4; u < 8; ++u)
+                    if (kb + u < nk) prefetch_l1(L + (size_t)(kb + u) * kWarp);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (kb + u >= nk) break;
@@ -320,7 +425,6 @@ __global__ void __launch_bounds__(256) k_adj_list(DevPlan dp)
         const float z10 = acc.sa - acc.sab, z01 = acc.sb - acc.sab;
         dp.zbuf[in.z_off + (size_t)it.group * w * w + cell] = make_float4(acc.s0 - acc.sa - z01, z10, z01, acc.sab);
     }
-    release_queue(ctr, lane);
 }
 
 template <typename T>
@@ -353,35 +457,65 @@ int adj_cells_blocks_per_sm()
     return nb;
 }
 
-int adj_list_blocks_per_sm(bool frac)
+namespace {
+const void* adj_list_fn(int lm)
+{
+    if (lm == 1) return reinterpret_cast<const void*>(k_adj_list<1>);
+    if (lm == 2) return reinterpret_cast<const void*>(k_adj_list<2>);
+    return reinterpret_cast<const void*>(k_adj_list<0>);
+}
+} // namespace
+
+int adj_list_blocks_per_sm(int lm)
 {
     int nb = 0;
-    const void* fn = frac ? reinterpret_cast<const void*>(k_adj_list<true>)
-                          : reinterpret_cast<const void*>(k_adj_list<false>);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, adj_list_fn(lm), 256, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return nb;
 }
 
-cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
-                             uint32_t* out, bool frac, cudaStream_t st)
+cudaError_t launch_adj_frac_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
+                                  uint32_t* out, cudaStream_t st)
 {
     const int cells = (n + 1) * (n + 1);
     const int blocks = (cells + 255) / 256;
     if (!out) k_adj_build<0><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
-    else if (frac) k_adj_build<2><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
-    else k_adj_build<1><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
+    else k_adj_build<2><<<blocks, 256, 0, st>>>(dp, inst_idx, counts, pbase, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_seg(const DevPlan& dp, int inst_idx, int n, bool pairs, int jblock, int nblk, int32_t* seg,
+                           const int64_t* pbase, uint32_t* out, cudaStream_t st)
+{
+    const int cells = (n + 1) * (n + 1);
+    const int blocks = (cells + 255) / 256;
+    if (!out) {
+        if (pairs) k_adj_seg<true, false><<<blocks, 256, 0, st>>>(dp, inst_idx, jblock, nblk, seg, pbase, out);
+        else k_adj_seg<false, false><<<blocks, 256, 0, st>>>(dp, inst_idx, jblock, nblk, seg, pbase, out);
+    } else {
+        if (pairs) k_adj_seg<true, true><<<blocks, 256, 0, st>>>(dp, inst_idx, jblock, nblk, seg, pbase, out);
+        else k_adj_seg<false, true><<<blocks, 256, 0, st>>>(dp, inst_idx, jblock, nblk, seg, pbase, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    k_fill_u32<<<(unsigned)blocks, 256, 0, st>>>(p, n, v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_cells(const DevPlan& dp, cudaStream_t st)
 {
-    if (dp.adj_mode == 1 || dp.adj_mode == 3) {
-        if (dp.n_list_items == 0) return cudaSuccess;
-        if (dp.adj_mode == 3) return launch_pdl(k_adj_list<true>, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);
-        return launch_pdl(k_adj_list<false>, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);
+    if (dp.adj_mode == 1 || dp.adj_mode == 3 || dp.adj_mode == 4) {
+        if (dp.n_list_items == 0) return cudaSuccess;   // (cell_blocks x 8 warps run the items)
+        if (dp.adj_mode == 3) return launch_pdl(k_adj_list<1>, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);
+        if (dp.adj_mode == 4) return launch_pdl(k_adj_list<2>, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);
+        return launch_pdl(k_adj_list<0>, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);
     }
     if (dp.n_cell_items == 0) return cudaSuccess;
     return launch_pdl(k_adj_cells, dim3(dp.cell_blocks), dim3(256), 0, st, 1, dp);

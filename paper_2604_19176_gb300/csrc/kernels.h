@@ -80,14 +80,25 @@ cudaError_t launch_count_samples(const DevPlan& dp, int inst_idx, int n_det, uns
 // adjoint cell kernel (256-thread CTAs).
 int circmean_blocks_per_sm(int m_lanes, bool bf16, int smem_bytes);
 int adj_cells_blocks_per_sm();
-int adj_list_blocks_per_sm(bool frac);
+// Resident CTAs per SM of the list gather: lm 0 = code lists, 1 = fraction
+// lists, 2 = run-pair code lists.
+int adj_list_blocks_per_sm(int lm);
 
-// Adjoint list building at plan creation: counts the hits of every cell of
-// instance inst_idx into `counts` (out == nullptr), or, given the cells'
-// padded list starts `start` (entries), fills the lists as packed codes
-// (4 B per entry) or, with fa / fb, as weight indices plus the fractions
-// a, b (12 B per entry).
-cudaError_t launch_adj_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
-                             uint32_t* out, bool frac, cudaStream_t st);
+// Fraction-list building at plan creation (layouts in pat_internal.h):
+// counts the samples of every cell of instance inst_idx into `counts`
+// (out == nullptr), or fills the lists given the (patch, part) block bases.
+cudaError_t launch_adj_frac_build(const DevPlan& dp, int inst_idx, int n, int32_t* counts, const int64_t* pbase,
+                                  uint32_t* out, cudaStream_t st);
+
+// Code-list building: with out == nullptr, atomicMax of every cell's entry
+// count per detector block into seg (per patch: nblk blocks + 1, zeroed by
+// the caller); else writes every entry at its aligned position (seg holding
+// the segment starts and each patch's length in vectors, out pre-filled
+// with null codes).  pairs: run-pair codes.
+cudaError_t launch_adj_seg(const DevPlan& dp, int inst_idx, int n, bool pairs, int jblock, int nblk, int32_t* seg,
+                           const int64_t* pbase, uint32_t* out, cudaStream_t st);
+
+// p[0 .. n) = v
+cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t st);
 
 } // namespace patgpu

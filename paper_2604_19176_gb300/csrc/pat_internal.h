@@ -39,8 +39,8 @@ constexpr int kPatchW = 8;        // adjoint: one warp owns an 8 x 4 patch of ce
 constexpr int kPatchH = 4;
 // Work queues live kQueueStride ints apart (one 128-byte line each, so that
 // queues taken by different CTAs do not serialise on one L2 line): queue 0 is
-// the adjoint cell kernel's, queue 1 the adjoint list kernel's.  Each queue
-// is two ints: the next item and the count of finished participants.
+// the adjoint cell kernel's (the list kernel's schedule is static).  Each
+// queue is two ints: the next item and the count of finished participants.
 constexpr int kQueueStride = 32;
 
 // Per-instance descriptor (device resident, read by every kernel).
@@ -112,14 +112,39 @@ struct CellItem {
     int32_t inst, x0, y0, group;
 };
 
-// Adjoint lists.  Cell c of an instance (cells numbered (cy + 1) * (n + 1) +
-// cx + 1) has count[c] samples in the order (j, q, m), grouped in vectors of
-// four (the last one padded with null entries: weight index of the
-// always-zero column m_pitch - 1 of row 0) and split into G parts of
-// consecutive vectors.  Part g of the 32 cells of an 8 x 4 patch is one block
-// of 16-byte slots: vector k of the cell in lane l at slot base + k * 32 + l
-// (code lists), or base + (3 k + s) * 32 + l for fraction lists (s = 0: Mbar
-// indices, 1: a, 2: b), each block as long as the patch's longest part.
+// Adjoint lists.  Cells are numbered (cy + 1) * (n + 1) + cx + 1; one warp
+// item is (8 x 4 patch of cells, part), lane = cell, and every list is kept
+// in 16-byte vectors of four entries, the 32 cells' vectors interleaved:
+// vector k of the cell in lane l at slot base + k * 32 + l (code lists), or
+// base + (3 k + s) * 32 + l for fraction lists (s = 0: Mbar indices, 1: a,
+// 2: b).  list_base gives the first slot of each (patch, part) block, and one
+// more entry after the last block (the kernel reads bases and lengths from
+// its ListItem records).
+//   Code lists (adj_mode 1, 4): a patch's entries are aligned by detector
+// blocks of jblock detectors: the entries of block b (in the order (j, q, m))
+// of every cell of the patch start at the same position, the block's
+// segment as long as the patch's longest, shorter cells padded with null
+// entries (weight index of the always-zero column m_pitch - 1 of row 0), so
+// that the 32 lanes of a warp read the detector, ray and Mbar entries of at
+// most jblock detectors at a time.  The patch's sequence (padded to whole
+// vectors) is split into G parts of consecutive vectors, the same for every
+// lane: a block holds (its length in vectors) x 32 slots.  An entry is
+// q << (jb + mb) | j << mb | m (one sample) or, in run-pair lists (adj_mode
+// 4), the same with bit 31 set for two samples of one ray at radii m, m + 1.
+//   Fraction lists (adj_mode 3): cell c has count[c] samples in the order
+// (j, q, m), in vectors padded at the end with null entries, each cell's
+// vectors split into G parts (part g holds vectors [g nv / G, (g + 1) nv / G)
+// of a cell with nv vectors); a block is as long as the patch's longest part.
+
+// Item of the list gather: part `group` of the 8 x 4 patch with lower-left
+// cell (x0, y0) of instance inst, whose block starts at 16-byte slot `base`
+// and holds nk vectors per lane (code lists; the longest lane's for
+// fraction lists).  Items are assigned to warps at plan time (LPT by nk);
+// warp w runs warp_items[w] .. warp_items[w + 1] - 1.  32 bytes.
+struct ListItem {
+    int64_t base;
+    int32_t nk, inst, group, x0, y0, pad;
+};
 
 // Tile of the elementwise / stencil kernels: 32 x 8 pixels.
 struct ImgTile {
@@ -145,9 +170,10 @@ struct DevPlan {
     const ImgTile* img_tiles;
     const TimeGroup* time_groups;  // fused time stage groups, most work first
     const int64_t* list_base;      // adjoint lists: first 16-byte slot of each (patch, part) block
-    const int32_t* cell_cnt;       // adjoint lists: samples of each cell
+    const int32_t* cell_cnt;       // adjoint fraction lists: samples of each cell
     const uint32_t* codes;         // adjoint lists: the blocks (codes, or indices and fractions)
-    const CellItem* list_items;    // adjoint list mode: (patch, part) items, longest part first
+    const ListItem* list_items;    // adjoint list mode: (patch, part) items, grouped by warp
+    const int32_t* warp_items;     // adjoint list mode: first item of each warp (+ end)
     float* mpart;                  // forward partial slots
     float* msum;                   // forward circular-mean sums M (same layout as Mbar)
     int32_t* work_counters;        // dynamic work queues, kQueueStride ints apart (see kQueueStride)
@@ -160,7 +186,9 @@ struct DevPlan {
     int32_t n_msum_rows;           // rows of M over all instances
     int32_t n_r_max;               // largest n_r of any instance
     int32_t m_lanes, adj_groups;
-    int32_t adj_mode;              // 3 = fraction lists, 1 = code lists, 0 = compute mode
+    int32_t adj_mode;              // 4 = run-pair code lists, 3 = fraction lists, 1 = code lists,
+                                   //   0 = compute mode
+    int32_t adj_jblock;            // code lists: detectors per aligned block
     int32_t cell_blocks;           // CTAs of the adjoint cell kernel (8 warps each)
     int32_t fwd_smem_bytes;        // dynamic shared memory of the circular-mean kernel
     int32_t fwd_rays_off;          // byte offset of the staged rays (after the largest tile)

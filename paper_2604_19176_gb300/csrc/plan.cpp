@@ -584,20 +584,27 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                 slot_samples_all += tmpls[inst_tmpl[i]].slot_samples;
             }
     }
-    // packed code lists (4 B per sample) when the code bits and the budget
-    // allow (the fastest form measured), else fraction lists (12 B per
-    // sample), else enumeration on every call
-    const bool codes_fit = P.code_bits_max <= 32;
+    // packed code lists (4 B per sample; run pairs when a code has a bit to
+    // spare) when the code bits and the budget allow (the fastest form
+    // measured), else fraction lists (12 B per sample), else enumeration on
+    // every call
+    const bool codes_fit = P.code_bits_max <= 32, pairs_fit = P.code_bits_max <= 31;
     if (opt.adj_mode == 1 && !codes_fit) return PAT_ERR_UNSUPPORTED;
+    if (opt.adj_mode == 4 && !pairs_fit) return PAT_ERR_UNSUPPORTED;
     int list_mode = opt.adj_mode;
     if (list_mode == 0) {
+        // (aligned code lists: the budget allows for their null entries)
         const double budget = (double)P.list_budget_bytes;
-        list_mode = codes_fit && (double)slot_samples_all * 4.0 <= budget ? 1
-                    : (double)slot_samples_all * 12.0 <= budget            ? 3
-                                                                           : 2;
+        list_mode = codes_fit && (double)slot_samples_all * 4.0 * 1.5 <= budget ? (pairs_fit ? 4 : 1)
+                    : (double)slot_samples_all * 12.0 <= budget                  ? 3
+                                                                                 : 2;
     }
-    const bool use_lists = list_mode == 1 || list_mode == 3;
+    const bool use_lists = list_mode == 1 || list_mode == 3 || list_mode == 4;
     const bool frac_lists = list_mode == 3;
+    const int list_lm = list_mode == 3 ? 1 : list_mode == 4 ? 2 : 0;
+    // detectors per aligned block of the code lists (measured best at 8 on
+    // the 256^2 - 760^2 workloads; the autotuner tries others)
+    const int jblock = use_lists && !frac_lists ? (opt.adj_jblock > 0 ? opt.adj_jblock : 8) : 0;
     int AG = opt.adj_groups;
     if (AG == 0) AG = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * resident_warps + patches - 1) / patches));
     // Items with an estimate of their cost (candidate rays per detector, from
@@ -626,7 +633,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     // each), enough (patch, part) items for about two per resident warp
     int LG = 1;
     if (use_lists) {
-        const int lbps = adj_list_blocks_per_sm(frac_lists);
+        const int lbps = adj_list_blocks_per_sm(list_lm);
         if (lbps < 1) return PAT_ERR_UNSUPPORTED;
         const int64_t lres = (int64_t)lbps * P.num_sms * 8;
         LG = opt.adj_groups > 0 ? opt.adj_groups
@@ -867,75 +874,149 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     }
 
     // ---- adjoint sample lists (list mode) --------------------------------------
-    // Hits are counted per cell, then stored per (8 x 4 patch, part): the 32
-    // cells' parts interleaved vector by vector, each block as long as the
-    // patch's longest part (layout in pat_internal.h, fill in k_adj_build).
+    // Per (8 x 4 patch, part): the 32 cells' parts interleaved vector by
+    // vector (layouts in pat_internal.h).  Fraction lists: hits counted per
+    // cell, each block as long as the patch's longest part (fill in
+    // k_adj_build).  Code lists: per (patch, detector block) the longest entry
+    // count of the patch's cells sets the block's segment; the segments make
+    // the patch's sequence, cut into G equal parts (fill in k_adj_seg).
     int64_t list_bytes = 0;
     if (use_lists) {
         const int S = frac_lists ? 3 : 1;     // 16-byte slots per vector of four entries
         const int G = LG;
-        dp.adj_groups = G;                    // the fill kernel splits lists into G parts
-        // count the hits of every cell, per geometry template (first instance)
-        std::vector<int> rep(tmpls.size(), -1);
+        dp.adj_groups = G;                    // the fill kernels split lists into G parts
+        std::vector<int> rep(tmpls.size(), -1);   // first instance of each geometry template
         for (int i = 0; i < n_inst; ++i)
             if (rep[inst_tmpl[i]] < 0) rep[inst_tmpl[i]] = i;
-        std::vector<std::vector<int32_t>> counts(tmpls.size());
-        int32_t* d_counts = nullptr;
-        int64_t max_cells = 0;
-        for (size_t t = 0; t < tmpls.size(); ++t)
-            max_cells = std::max<int64_t>(max_cells, (int64_t)(inst[rep[t]].n + 1) * (inst[rep[t]].n + 1));
-        if (cudaMalloc(&d_counts, sizeof(int32_t) * max_cells) != cudaSuccess) {
-            cudaGetLastError();
-            return PAT_ERR_OOM;
+        for (size_t t = 0; t < tmpls.size(); ++t) {
+            const int w = inst[rep[t]].n + 1;
+            for (int i = 0; i < n_inst; ++i)
+                if (inst_tmpl[i] == (int)t) inst[i].patches_x = (w + kPatchW - 1) / kPatchW;
         }
-        pat_status_t s = PAT_OK;
-        for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
-            const int i = rep[t];
-            const int cells = (inst[i].n + 1) * (inst[i].n + 1);
-            if (launch_adj_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, false, st) != cudaSuccess)
-                s = PAT_ERR_CUDA;
-            counts[t].resize(cells);
-            if (s == PAT_OK && cudaMemcpyAsync(counts[t].data(), d_counts, sizeof(int32_t) * cells,
+        if (cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(InstDev) * inst.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+            return PAT_ERR_CUDA;
+        std::vector<int32_t> cnt_all;             // fraction lists: samples per cell
+        std::vector<int64_t> tmpl_cnt_off(tmpls.size(), 0), tmpl_pbase_off(tmpls.size());
+        std::vector<std::vector<int32_t>> part_len(tmpls.size());
+        std::vector<int64_t> pbase_all;
+        std::vector<int> nblk(tmpls.size(), 0);   // code lists: detector blocks per template
+        int32_t* d_seg = nullptr;                 // code lists: per patch, segment starts + length (fill only)
+        std::vector<int64_t> seg_off(tmpls.size() + 1, 0), slot0(tmpls.size() + 1, 0);
+        int64_t slots_total = 0;   // 16-byte slots
+        if (frac_lists) {
+            std::vector<std::vector<int32_t>> counts(tmpls.size());
+            int32_t* d_counts = nullptr;
+            int64_t max_cells = 0;
+            for (size_t t = 0; t < tmpls.size(); ++t)
+                max_cells = std::max<int64_t>(max_cells, (int64_t)(inst[rep[t]].n + 1) * (inst[rep[t]].n + 1));
+            if (cudaMalloc(&d_counts, sizeof(int32_t) * max_cells) != cudaSuccess) {
+                cudaGetLastError();
+                return PAT_ERR_OOM;
+            }
+            pat_status_t s = PAT_OK;
+            for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
+                const int i = rep[t];
+                const int cells = (inst[i].n + 1) * (inst[i].n + 1);
+                if (launch_adj_frac_build(dp, i, inst[i].n, d_counts, nullptr, nullptr, st) != cudaSuccess)
+                    s = PAT_ERR_CUDA;
+                counts[t].resize(cells);
+                if (s == PAT_OK && cudaMemcpyAsync(counts[t].data(), d_counts, sizeof(int32_t) * cells,
+                                                   cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    s = PAT_ERR_CUDA;
+                if (s == PAT_OK && cudaStreamSynchronize(st) != cudaSuccess) s = PAT_ERR_CUDA;
+            }
+            cudaFree(d_counts);
+            if (s != PAT_OK) return s;
+            for (size_t t = 0; t < tmpls.size(); ++t) {
+                const int n = inst[rep[t]].n, w = n + 1;
+                const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
+                tmpl_cnt_off[t] = (int64_t)cnt_all.size();
+                cnt_all.insert(cnt_all.end(), counts[t].begin(), counts[t].end());
+                tmpl_pbase_off[t] = (int64_t)pbase_all.size();
+                part_len[t].assign((size_t)pw * ph * G, 0);
+                for (int py = 0; py < ph; ++py)
+                    for (int px = 0; px < pw; ++px)
+                        for (int g = 0; g < G; ++g) {
+                            int V = 0;
+                            for (int dy = 0; dy < kPatchH; ++dy)
+                                for (int dx = 0; dx < kPatchW; ++dx) {
+                                    const int cxa = px * kPatchW + dx, cya = py * kPatchH + dy;   // cell + 1
+                                    if (cxa >= w || cya >= w) continue;
+                                    const int nv = (counts[t][(size_t)cya * w + cxa] + 3) >> 2;
+                                    const int v0 = (int)((int64_t)g * nv / G), v1 = (int)((int64_t)(g + 1) * nv / G);
+                                    V = std::max(V, v1 - v0);
+                                }
+                            part_len[t][((size_t)py * pw + px) * G + g] = V;
+                            pbase_all.push_back(slots_total);
+                            slots_total += (int64_t)V * S * kWarp;
+                        }
+            }
+        } else {
+            // longest entry count per (patch, detector block), per template
+            for (size_t t = 0; t < tmpls.size(); ++t) {
+                const int w = inst[rep[t]].n + 1;
+                const int64_t patches_t = (int64_t)((w + kPatchW - 1) / kPatchW) * ((w + kPatchH - 1) / kPatchH);
+                nblk[t] = (inst[rep[t]].n_det + jblock - 1) / jblock;
+                seg_off[t + 1] = seg_off[t] + patches_t * (nblk[t] + 1);
+            }
+            if (cudaMalloc(&d_seg, sizeof(int32_t) * std::max<int64_t>(seg_off.back(), 1)) != cudaSuccess) {
+                cudaGetLastError();
+                return PAT_ERR_OOM;
+            }
+            pat_status_t s = PAT_OK;
+            if (cudaMemsetAsync(d_seg, 0, sizeof(int32_t) * seg_off.back(), st) != cudaSuccess) s = PAT_ERR_CUDA;
+            for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
+                const int i = rep[t];
+                if (launch_adj_seg(dp, i, inst[i].n, list_mode == 4, jblock, nblk[t], d_seg + seg_off[t], nullptr,
+                                   nullptr, st) != cudaSuccess)
+                    s = PAT_ERR_CUDA;
+            }
+            std::vector<int32_t> seg_host(seg_off.back());
+            if (s == PAT_OK && cudaMemcpyAsync(seg_host.data(), d_seg, sizeof(int32_t) * seg_host.size(),
                                                cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 s = PAT_ERR_CUDA;
             if (s == PAT_OK && cudaStreamSynchronize(st) != cudaSuccess) s = PAT_ERR_CUDA;
-        }
-        cudaFree(d_counts);
-        if (s != PAT_OK) return s;
-        // block bases per (template, patch, part) and the longest part of each
-        std::vector<int32_t> cnt_all;
-        std::vector<int64_t> pbase_all;
-        std::vector<int64_t> tmpl_cnt_off(tmpls.size()), tmpl_pbase_off(tmpls.size());
-        std::vector<std::vector<int32_t>> part_len(tmpls.size());
-        int64_t slots_total = 0;   // 16-byte slots
-        for (size_t t = 0; t < tmpls.size(); ++t) {
-            const int n = inst[rep[t]].n, w = n + 1;
-            const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
-            tmpl_cnt_off[t] = (int64_t)cnt_all.size();
-            cnt_all.insert(cnt_all.end(), counts[t].begin(), counts[t].end());
-            tmpl_pbase_off[t] = (int64_t)pbase_all.size();
-            part_len[t].assign((size_t)pw * ph * G, 0);
-            for (int py = 0; py < ph; ++py)
-                for (int px = 0; px < pw; ++px)
-                    for (int g = 0; g < G; ++g) {
-                        int V = 0;
-                        for (int dy = 0; dy < kPatchH; ++dy)
-                            for (int dx = 0; dx < kPatchW; ++dx) {
-                                const int cxa = px * kPatchW + dx, cya = py * kPatchH + dy;   // cell + 1
-                                if (cxa >= w || cya >= w) continue;
-                                const int nv = (counts[t][(size_t)cya * w + cxa] + 3) >> 2;
-                                const int v0 = (int)((int64_t)g * nv / G), v1 = (int)((int64_t)(g + 1) * nv / G);
-                                V = std::max(V, v1 - v0);
-                            }
-                        part_len[t][((size_t)py * pw + px) * G + g] = V;
-                        pbase_all.push_back(slots_total);
-                        slots_total += (int64_t)V * S * kWarp;
+            // segment starts, each patch's length in vectors, and the parts
+            for (size_t t = 0; t < tmpls.size() && s == PAT_OK; ++t) {
+                const int w = inst[rep[t]].n + 1;
+                const int pw = (w + kPatchW - 1) / kPatchW, ph = (w + kPatchH - 1) / kPatchH;
+                const int nb = nblk[t];
+                tmpl_pbase_off[t] = (int64_t)pbase_all.size();
+                slot0[t] = slots_total;
+                part_len[t].assign((size_t)pw * ph * G, 0);
+                for (int64_t pi = 0; pi < (int64_t)pw * ph; ++pi) {
+                    int32_t* sp = seg_host.data() + seg_off[t] + pi * (nb + 1);
+                    int64_t start = 0;
+                    for (int b = 0; b < nb; ++b) {
+                        const int32_t len = sp[b];
+                        sp[b] = (int32_t)start;
+                        start += len;
                     }
-            for (int i = 0; i < n_inst; ++i)
-                if (inst_tmpl[i] == (int)t) inst[i].patches_x = pw;
+                    if (start > INT32_MAX - 3) s = PAT_ERR_UNSUPPORTED;
+                    const int nv = (int)((start + 3) >> 2);
+                    sp[nb] = nv;
+                    for (int g = 0; g < G; ++g) {
+                        const int V = (int)((int64_t)(g + 1) * nv / G) - (int)((int64_t)g * nv / G);
+                        part_len[t][(size_t)pi * G + g] = V;
+                        pbase_all.push_back(slots_total);
+                        slots_total += (int64_t)V * kWarp;
+                    }
+                }
+            }
+            slot0[tmpls.size()] = slots_total;
+            if (s == PAT_OK && cudaMemcpyAsync(d_seg, seg_host.data(), sizeof(int32_t) * seg_host.size(),
+                                               cudaMemcpyHostToDevice, st) != cudaSuccess)
+                s = PAT_ERR_CUDA;
+            if (s != PAT_OK) {
+                cudaStreamSynchronize(st);
+                cudaFree(d_seg);
+                return s;
+            }
         }
-        // work items: (patch, part), longest part first
-        std::vector<std::pair<int32_t, CellItem>> li;
+        pbase_all.push_back(slots_total);   // end of the last block
+        // work items: (patch, part) with their block and length
+        std::vector<ListItem> li;
         for (int i = 0; i < n_inst; ++i) {
             const int t = inst_tmpl[i];
             const int n = inst[i].n, w = n + 1;
@@ -943,59 +1024,130 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             for (int py = 0; py < ph; ++py)
                 for (int px = 0; px < pw; ++px)
                     for (int g = 0; g < G; ++g) {
-                        const int32_t V = part_len[t][((size_t)py * pw + px) * G + g];
-                        if (V > 0) li.push_back({V, CellItem{i, px * kPatchW - 1, py * kPatchH - 1, g}});
+                        const size_t pi = ((size_t)py * pw + px) * G + g;
+                        const int32_t V = part_len[t][pi];
+                        if (V > 0)
+                            li.push_back(ListItem{pbase_all[tmpl_pbase_off[t] + pi], V, i, g, px * kPatchW - 1,
+                                                  py * kPatchH - 1, 0});
                     }
         }
-        std::stable_sort(li.begin(), li.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+        // static schedule: items to the warps of the launch, longest first to
+        // the least loaded warp (a vector costs the same everywhere; an item
+        // start costs about one vector more), then each warp's items in
+        // (instance, patch) order
+        const int lbps = adj_list_blocks_per_sm(list_lm);
+        if (lbps < 1) {
+            if (d_seg) {
+                cudaStreamSynchronize(st);
+                cudaFree(d_seg);
+            }
+            return PAT_ERR_UNSUPPORTED;
+        }
+        const int lblocks = (int)std::max<int64_t>(
+            1, std::min<int64_t>((int64_t)lbps * P.num_sms, ((int64_t)li.size() + 7) / 8));
+        const int n_warps = lblocks * 8;
+        std::vector<int32_t> warp_items(n_warps + 1, 0);
+        std::vector<ListItem> sched(li.size());
+        {
+            std::vector<int32_t> order(li.size());
+            for (size_t k = 0; k < li.size(); ++k) order[k] = (int32_t)k;
+            std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return li[a].nk > li[b].nk; });
+            using Load = std::pair<int64_t, int32_t>;   // (cost, warp)
+            std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+            for (int wv = 0; wv < n_warps; ++wv) heap.push({0, wv});
+            std::vector<int32_t> owner(li.size());
+            for (int32_t k : order) {
+                Load l = heap.top();
+                heap.pop();
+                owner[k] = l.second;
+                l.first += li[k].nk + 1;
+                heap.push(l);
+            }
+            for (size_t k = 0; k < li.size(); ++k) ++warp_items[owner[k] + 1];
+            for (int wv = 0; wv < n_warps; ++wv) warp_items[wv + 1] += warp_items[wv];
+            std::vector<int32_t> fill(warp_items.begin(), warp_items.end() - 1);
+            for (size_t k = 0; k < li.size(); ++k) sched[fill[owner[k]]++] = li[k];   // (li is in patch order)
+        }
         const size_t b_pbase = sizeof(int64_t) * std::max<size_t>(pbase_all.size(), 1);
-        const size_t b_cnt = sizeof(int32_t) * cnt_all.size();
-        const size_t b_items = sizeof(CellItem) * std::max<size_t>(li.size(), 1);
+        const size_t b_cnt = sizeof(int32_t) * std::max<size_t>(cnt_all.size(), 1);
+        const size_t b_items = sizeof(ListItem) * std::max<size_t>(sched.size(), 1);
+        const size_t b_witems = sizeof(int32_t) * warp_items.size();
         const size_t b_codes = 16 * (size_t)std::max<int64_t>(slots_total, 1);
         const size_t o_cnt_l = align(b_pbase), o_items_l = align(o_cnt_l + b_cnt);
-        const size_t o_codes_l = align(o_items_l + b_items);
+        const size_t o_witems_l = align(o_items_l + b_items);
+        const size_t o_codes_l = align(o_witems_l + b_witems);
         list_bytes = (int64_t)(o_codes_l + b_codes);
+        auto drop_seg = [&]() {   // (the segment table is only needed by the fill)
+            if (d_seg) {
+                cudaStreamSynchronize(st);
+                cudaFree(d_seg);
+                d_seg = nullptr;
+            }
+        };
         if (cudaMalloc(&P.d_lists, list_bytes) != cudaSuccess) {
             P.d_lists = nullptr;
             cudaGetLastError();
+            drop_seg();
             return PAT_ERR_OOM;
         }
         unsigned char* lb = static_cast<unsigned char*>(P.d_lists);
-        std::vector<CellItem> items(li.size());
-        for (size_t k = 0; k < li.size(); ++k) items[k] = li[k].second;
+        uint32_t* codes = reinterpret_cast<uint32_t*>(lb + o_codes_l);
         if (cudaMemcpyAsync(lb, pbase_all.data(), sizeof(int64_t) * pbase_all.size(), cudaMemcpyHostToDevice, st) !=
                 cudaSuccess ||
-            cudaMemcpyAsync(lb + o_cnt_l, cnt_all.data(), b_cnt, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(lb + o_items_l, items.data(), sizeof(CellItem) * items.size(), cudaMemcpyHostToDevice,
-                            st) != cudaSuccess ||
-            cudaMemsetAsync(lb + o_codes_l, 0, b_codes, st) != cudaSuccess)
+            (!cnt_all.empty() &&
+             cudaMemcpyAsync(lb + o_cnt_l, cnt_all.data(), sizeof(int32_t) * cnt_all.size(), cudaMemcpyHostToDevice,
+                             st) != cudaSuccess) ||
+            (!sched.empty() && cudaMemcpyAsync(lb + o_items_l, sched.data(), sizeof(ListItem) * sched.size(),
+                                               cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+            cudaMemcpyAsync(lb + o_witems_l, warp_items.data(), b_witems, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemsetAsync(codes, 0, b_codes, st) != cudaSuccess) {
+            drop_seg();
             return PAT_ERR_CUDA;
+        }
         dp.list_base = reinterpret_cast<const int64_t*>(lb);
-        dp.cell_cnt = reinterpret_cast<const int32_t*>(lb + o_cnt_l);
-        dp.list_items = reinterpret_cast<const CellItem*>(lb + o_items_l);
-        dp.codes = reinterpret_cast<const uint32_t*>(lb + o_codes_l);
+        dp.cell_cnt = frac_lists ? reinterpret_cast<const int32_t*>(lb + o_cnt_l) : nullptr;
+        dp.list_items = reinterpret_cast<const ListItem*>(lb + o_items_l);
+        dp.warp_items = reinterpret_cast<const int32_t*>(lb + o_witems_l);
+        dp.codes = codes;
         for (int i = 0; i < n_inst; ++i) {
             inst[i].list_off = tmpl_cnt_off[inst_tmpl[i]];
             inst[i].pbase_off = tmpl_pbase_off[inst_tmpl[i]];
         }
         if (cudaMemcpyAsync(base + o_inst, inst.data(), sizeof(InstDev) * inst.size(), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess)
+            cudaSuccess) {
+            drop_seg();
             return PAT_ERR_CUDA;
-        // fill the lists (same enumeration, same order; null entries end each cell's last vector)
+        }
+        // fill the lists (same enumeration, same order)
         for (size_t t = 0; t < tmpls.size(); ++t) {
             const int i = rep[t];
-            if (launch_adj_build(dp, i, inst[i].n, const_cast<int32_t*>(dp.cell_cnt) + tmpl_cnt_off[t],
-                                 dp.list_base + tmpl_pbase_off[t], reinterpret_cast<uint32_t*>(lb + o_codes_l),
-                                 frac_lists, st) != cudaSuccess)
+            cudaError_t e;
+            if (frac_lists) {
+                e = launch_adj_frac_build(dp, i, inst[i].n, const_cast<int32_t*>(dp.cell_cnt) + tmpl_cnt_off[t],
+                                          dp.list_base + tmpl_pbase_off[t], codes, st);
+            } else {
+                // null codes (row 0, the always-zero column m_pitch - 1) everywhere first
+                const int64_t s0 = slot0[t], s1 = slot0[t + 1];
+                e = launch_fill_u32(codes + s0 * 4, (s1 - s0) * 4, (uint32_t)inst[i].m_pitch - 1u, st);
+                if (e == cudaSuccess)
+                    e = launch_adj_seg(dp, i, inst[i].n, list_mode == 4, jblock, nblk[t], d_seg + seg_off[t],
+                                       dp.list_base + tmpl_pbase_off[t], codes, st);
+            }
+            if (e != cudaSuccess) {
+                drop_seg();
                 return PAT_ERR_CUDA;
+            }
         }
-        if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            drop_seg();
+            return PAT_ERR_CUDA;
+        }
+        drop_seg();
         dp.n_list_items = (int)li.size();
-        dp.adj_mode = frac_lists ? 3 : 1;
-        const int lbps = adj_list_blocks_per_sm(frac_lists);
-        if (lbps < 1) return PAT_ERR_UNSUPPORTED;
-        dp.cell_blocks = (int)std::max<int64_t>(
-            1, std::min<int64_t>((int64_t)lbps * P.num_sms, ((int64_t)li.size() + 7) / 8));
+        dp.adj_mode = list_mode;
+        dp.adj_jblock = jblock;
+        dp.cell_blocks = lblocks;
     }
 
     // ---- info -------------------------------------------------------------
@@ -1024,6 +1176,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     I.abel_split_fwd = dp.abel_cluster_fwd;
     I.abel_split_adj = dp.abel_cluster_adj;
     I.time_pair = dp.time_chunks > 0 ? 1 : 0;
+    I.adj_jblock = dp.adj_jblock;
     I.list_bytes = list_bytes;
     I.device_bytes += list_bytes;
     I.bands_max = tiles_max;

@@ -47,6 +47,7 @@ std::string tune_key(const pat_geometry_t* geoms, int n, const pat_options_t& op
     put(&opt.image_dtype, sizeof opt.image_dtype);
     put(&opt.adj_mode, sizeof opt.adj_mode);
     put(&opt.time_pair, sizeof opt.time_pair);
+    put(&opt.adj_jblock, sizeof opt.adj_jblock);
     put(&device, sizeof device);
     return k;
 }
@@ -202,12 +203,23 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
     best_ms = 1e30f;
     pat_options_t fwd_opt = best_opt;
     // the list modes cut each cell's list into groups, the enumeration mode its detectors
-    std::vector<std::pair<int, int>> adj_cands;
-    for (int gcount : {0, 1, 2, 4, 8}) adj_cands.push_back({opt.adj_mode, gcount});
+    // (and, when not fixed, the detector block size of the aligned code lists)
+    struct AdjCand {
+        int groups, jblock;
+    };
+    std::vector<AdjCand> adj_cands;
+    // (16384: one block, i.e. every lane's list from the patch's first position)
+    const std::vector<int> jb_c = opt.adj_jblock > 0 ? std::vector<int>{opt.adj_jblock}
+                                  : large           ? std::vector<int>{8, 16}
+                                                    : std::vector<int>{4, 8, 16, 16384};
+    const std::vector<int> g_c = large ? std::vector<int>{0, 4, 8} : std::vector<int>{0, 1, 2, 4, 8};
+    for (int gcount : g_c)
+        for (int jb : jb_c) adj_cands.push_back({gcount, jb});
     for (auto& ac : adj_cands) {
         pat_options_t o = fwd_opt;
-        o.adj_mode = ac.first;
-        o.adj_groups = ac.second;
+        o.adj_mode = opt.adj_mode;
+        o.adj_groups = ac.groups;
+        o.adj_jblock = ac.jblock;
         Plan* p = try_build(geoms, n_inst, o, st);
         if (!p) continue;
         const float ms = time_ms(st, 2, 5, [&] {

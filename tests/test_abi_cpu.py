@@ -59,6 +59,10 @@ def test_host_validation_without_gpu(lib):
     opt = _lib.PatOptions()
     opt.m_lanes = 5
     assert lib.pat_plan_create(ctypes.byref(geom), 1, ctypes.byref(opt), None, ctypes.byref(h)) == 1
+    for field, value in (("adj_mode", 5), ("adj_mode", -1), ("adj_jblock", -1), ("adj_jblock", 16385)):
+        opt = _lib.PatOptions()
+        setattr(opt, field, value)
+        assert lib.pat_plan_create(ctypes.byref(geom), 1, ctypes.byref(opt), None, ctypes.byref(h)) == 1
     # calls on a handle that is not a live plan
     assert lib.pat_forward(None, None, None, None) == 6
     assert lib.pat_adjoint(ctypes.c_void_p(12345), None, None, None) == 6

@@ -91,7 +91,7 @@ def test_vessel1024_b8_full_size(cuda_dev, dtype):
     plan = PatPlan(geoms, device=cuda_dev, image_dtype=dtype, tune=1)
     info = plan.info()
     if dtype == torch.float32:
-        assert info["adj_mode"] == 1          # packed code lists: 9 + 12 + 11 = 32 bits per code
+        assert info["adj_mode"] == 1          # one-sample code lists: 9 + 12 + 11 = 32 bits per code (no pair bit)
     ft = torch.tensor(phs, dtype=dtype, device=cuda_dev)
     f_in = ft.double().cpu().numpy()
     gf = plan.forward(ft).double().cpu().numpy()

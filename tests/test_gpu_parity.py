@@ -79,7 +79,10 @@ def test_forward_adjoint_vessel256_full_size(cuda_dev):
 @pytest.mark.parametrize("kw", [dict(m_lanes=16), dict(m_lanes=8), dict(q_piece=4), dict(band_rows=5),
                                 dict(band_rows=17, m_lanes=8, q_piece=12), dict(adj_groups=1, adj_mode=2), dict(adj_groups=3, adj_mode=2),
                                 dict(adj_groups=16, adj_mode=2), dict(adj_mode=1), dict(adj_mode=1, adj_groups=3),
-                                dict(adj_mode=3), dict(adj_mode=3, adj_groups=5), dict(abel_split=1),
+                                dict(adj_mode=3), dict(adj_mode=3, adj_groups=5), dict(adj_mode=4),
+                                dict(adj_mode=4, adj_groups=3), dict(adj_mode=4, adj_jblock=1),
+                                dict(adj_mode=1, adj_jblock=3), dict(adj_mode=4, adj_jblock=64, adj_groups=16),
+                                dict(adj_mode=1, adj_jblock=5, adj_groups=7), dict(abel_split=1),
                                 dict(abel_split=2), dict(abel_split=8), dict(tune=1)])
 def test_tile_shapes_agree_with_oracle(cuda_dev, kw):
     g = Geometry(48, 24, 0.4, 1.3 * math.pi, 80, 2.0, 70)
@@ -321,15 +324,35 @@ def test_large_radius_positions_n384(cuda_dev):
     assert rel(run_adj(plan, d, cuda_dev), O.adjoint(og(g), d)) <= TOL
 
 
-def test_code_and_fraction_lists_agree_bitwise(cuda_dev):
-    """Fraction lists store the a, b that code lists recompute, in the same
-    order: with the same list split the two adjoints are bitwise equal."""
+def test_list_forms_agree_bitwise(cuda_dev):
+    """Every list form holds the same samples in the order (j, q, m): one-sample
+    codes, run-pair codes (a pair stands for radii m, m + 1 of one ray) at any
+    detector block size, and fraction lists (the a, b that the codes
+    recompute).  With one part per cell the moment sums then see the same
+    terms in the same order (null entries add exact zeros), so the adjoints
+    are bitwise equal."""
     g = Geometry(96, 40, 0.3, 1.5 * math.pi, 160, 2.0, 192)
     d = torch.tensor(inputs.random_data(40, 160, seed=61), dtype=torch.float32, device=cuda_dev)
     outs = []
-    for mode in (1, 3):
-        plan = PatPlan(g, device=cuda_dev, adj_mode=mode, adj_groups=3)
-        assert plan.info()["adj_mode"] == mode
+    for mode, jb in ((3, 0), (1, 8), (1, 1000), (4, 8), (4, 3), (4, 1)):
+        plan = PatPlan(g, device=cuda_dev, adj_mode=mode, adj_groups=1, adj_jblock=jb)
+        inf = plan.info()
+        assert inf["adj_mode"] == mode
+        assert inf["adj_jblock"] == (jb if mode != 3 else 0)
         outs.append(plan.adjoint(d).clone())
     torch.cuda.synchronize()
-    assert torch.equal(outs[0], outs[1])
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
+
+
+def test_run_pair_lists_split_in_parts(cuda_dev):
+    """With several parts per patch the part boundaries fall at other samples
+    for pair and one-sample codes; the adjoints then agree to FP32 rounding,
+    and a pair code list is shorter than the one-sample list."""
+    g = Geometry(96, 40, 0.3, 1.5 * math.pi, 160, 2.0, 192)
+    d = torch.tensor(inputs.random_data(40, 160, seed=61), dtype=torch.float32, device=cuda_dev)
+    p1 = PatPlan(g, device=cuda_dev, adj_mode=1, adj_groups=3, adj_jblock=8)
+    p4 = PatPlan(g, device=cuda_dev, adj_mode=4, adj_groups=3, adj_jblock=8)
+    a, b = p1.adjoint(d).double(), p4.adjoint(d).double()
+    assert float((a - b).norm() / a.norm()) <= 1e-6
+    assert p4.info()["list_bytes"] < 0.8 * p1.info()["list_bytes"]
