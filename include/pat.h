@@ -66,7 +66,8 @@ typedef enum {
     PAT_ERR_OOM = 3,         /* device or host allocation failed                */
     PAT_ERR_UNSUPPORTED = 4, /* valid request the library does not implement    */
     PAT_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
-    PAT_ERR_BAD_PLAN = 6     /* NULL, destroyed or foreign plan handle          */
+    PAT_ERR_BAD_PLAN = 6,    /* NULL, destroyed or foreign plan handle          */
+    PAT_ERR_BOUNDS = 7       /* a device-side bounds check failed (debug build) */
 } pat_status_t;
 
 typedef enum { PAT_F32 = 0, PAT_BF16 = 1 } pat_dtype_t;
@@ -295,7 +296,8 @@ pat_status_t pat_pdhg_step(pat_plan_t plan, float* d_f, float* d_fbar, float* d_
 
 /*
  * pat_plan_sync_status — synchronise the stream and report a device-side
- * error recorded by a bounded wait in a persistent launch (PAT_ERR_TIMEOUT),
+ * error recorded by a bounded wait in a persistent launch (PAT_ERR_TIMEOUT)
+ * or, in debug builds, by a failed bounds check (PAT_ERR_BOUNDS, see below),
  * clearing it.  Returns PAT_OK when none was recorded.
  * A launch whose wait gave up returns early: the results of that call are
  * undefined (some of its partial sums are missing), later calls are not
@@ -317,6 +319,36 @@ pat_status_t pat_plan_sync_status(pat_plan_t plan, void* stream);
  * return PAT_ERR_INVALID_ARG.  Synchronous with respect to the host only.
  */
 pat_status_t pat_plan_set_wait_probe(pat_plan_t plan, int32_t clocks);
+
+/*
+ * Debug builds.  Compiling the library with -DPAT_DEBUG (build.py:
+ * build(debug=True) makes libpatgpu_debug.so beside libpatgpu.so) adds
+ * device-side bounds checks to the hot kernels: the circular means check each
+ * work unit's detector, angle range and slot and each sample's staged-cell
+ * offset, the ray staging checks its shared-memory capacity, the fused time
+ * stage its staged rows and slot counts, and the list gather each item's code
+ * range and each entry's detector, ray and Mbar index.  A failed check skips
+ * the access, records the site in the plan's device status word (the first
+ * error is kept) and the kernel carries on; it never traps.  The results of
+ * that call are then undefined and pat_plan_sync_status reports
+ * PAT_ERR_BOUNDS once, clearing the word.  Release builds compile the checks
+ * out.  Such a check is the stand-in for a memory checker, which the GPUs
+ * this library is developed on do not offer.
+ *
+ * pat_debug_build — 1 when the library was compiled with -DPAT_DEBUG, else 0.
+ *
+ * pat_plan_set_bounds_probe — test hook for the checks above.  With enable
+ * != 0, the next adjoint gather of this plan (pat_adjoint, pat_tv_step,
+ * pat_pdhg_step) in code- or fraction-list form gives the first entry of its
+ * first warp's first item a detector index (and Mbar index) past the
+ * instance's detectors; everything that index would address still lies inside
+ * the plan's allocations, so nothing faults even where a check were missing.
+ * The entry check reports it and the entry is skipped.  The probe disarms
+ * itself after that one launch.  Returns PAT_ERR_UNSUPPORTED in release
+ * builds.  Synchronous with respect to the host only.
+ */
+int32_t pat_debug_build(void);
+pat_status_t pat_plan_set_bounds_probe(pat_plan_t plan, int32_t enable);
 
 /*
  * Per-kernel timing (tracing).  When enabled, every kernel the plan enqueues

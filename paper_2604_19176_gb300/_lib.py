@@ -11,11 +11,12 @@ import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libpatgpu.so")
+DEBUG_LIB_PATH = os.path.join(_PKG, "libpatgpu_debug.so")   # -DPAT_DEBUG build (build.build(debug=True))
 
 PAT_OK = 0
 STATUS_NAMES = {
     0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_CUDA", 3: "PAT_ERR_OOM",
-    4: "PAT_ERR_UNSUPPORTED", 5: "PAT_ERR_TIMEOUT", 6: "PAT_ERR_BAD_PLAN",
+    4: "PAT_ERR_UNSUPPORTED", 5: "PAT_ERR_TIMEOUT", 6: "PAT_ERR_BAD_PLAN", 7: "PAT_ERR_BOUNDS",
 }
 
 # Every symbol include/pat.h declares (checked by the CPU tests).
@@ -23,7 +24,7 @@ EXPORTED = (
     "pat_plan_create", "pat_plan_destroy", "pat_plan_layout", "pat_plan_info", "pat_forward",
     "pat_adjoint", "pat_tv_grad", "pat_residual", "pat_descent_step", "pat_plan_sync_status",
     "pat_plan_set_timing", "pat_plan_kernel_times", "pat_tv_grad_noalloc", "pat_tv_step", "pat_pdhg_step",
-    "pat_plan_set_wait_probe", "pat_status_string",
+    "pat_plan_set_wait_probe", "pat_status_string", "pat_debug_build", "pat_plan_set_bounds_probe",
 )
 KERNEL_KINDS = ("circmean", "abel_fwd", "abel_adj", "adjoint_gather", "tv", "residual", "descent", "tv_update",
                 "pdhg_dual", "pdhg_primal", "time_pair")
@@ -70,10 +71,18 @@ _lib = None
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load ``libpatgpu.so`` and declare the prototypes (raises if absent)."""
+    """Load ``libpatgpu.so`` (or another build of it, such as the debug build at
+    DEBUG_LIB_PATH) once per process and declare the prototypes; the operators
+    use whichever library was loaded first (raises if it is absent)."""
     global _lib
     if _lib is not None:
         return _lib
+    _lib = open_library(path)
+    return _lib
+
+
+def open_library(path: str) -> ctypes.CDLL:
+    """A separately loaded copy of a build of the library, with its prototypes."""
     if not os.path.exists(path):
         raise RuntimeError(
             f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
@@ -94,6 +103,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pat_plan_sync_status.argtypes = [vp, vp]
     lib.pat_plan_set_timing.argtypes = [vp, i32]
     lib.pat_plan_set_wait_probe.argtypes = [vp, i32]
+    lib.pat_plan_set_bounds_probe.argtypes = [vp, i32]
+    lib.pat_debug_build.argtypes = []
     lib.pat_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i64p, i32]
     lib.pat_tv_grad_noalloc.argtypes = [vp, i32, i32, f32, vp, vp, vp]
     lib.pat_tv_step.argtypes = [vp, vp, vp, vp, f32, f32, f32, i32, vp, vp]
@@ -103,7 +114,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in EXPORTED:
         if name != "pat_status_string":
             getattr(lib, name).restype = ctypes.c_int
-    _lib = lib
     return lib
 
 

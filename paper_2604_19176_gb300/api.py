@@ -282,6 +282,11 @@ class PatPlan:
         nothing completes, bounded by ``clocks`` SM cycles (see pat_plan_set_wait_probe)."""
         _lib.check("pat_plan_set_wait_probe", self._lib.pat_plan_set_wait_probe(self._h, int(clocks)))
 
+    def set_bounds_probe(self, enable: bool = True) -> None:
+        """Test hook of debug builds: the next list gather plants one out-of-range
+        detector index for its bounds check to report (see pat_plan_set_bounds_probe)."""
+        _lib.check("pat_plan_set_bounds_probe", self._lib.pat_plan_set_bounds_probe(self._h, 1 if enable else 0))
+
 
 def geometry_from(obj) -> Geometry:
     """Geometry from any object with the same fields (e.g. a dict)."""

@@ -2,7 +2,10 @@
 
 Each translation unit under ``csrc/`` is compiled in parallel into
 ``_build/`` and linked into ``paper_2604_19176_gb300/libpatgpu.so``.  Only
-sources newer than their object are recompiled.
+sources newer than their object are recompiled.  ``build(debug=True)``
+compiles the same sources with ``-DPAT_DEBUG`` (device-side bounds checks
+that report through the plan's status word, see include/pat.h) into
+``_build_debug/`` and ``libpatgpu_debug.so``.
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpatgpu.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libpatgpu_debug.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -41,18 +46,20 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    hdr = _headers_mtime()
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    flags = [*COMMON, "-DPAT_DEBUG"] if debug else COMMON
+    os.makedirs(bdir, exist_ok=True)
+    hdr = max(_headers_mtime(), os.path.getmtime(os.path.abspath(__file__)))
     jobs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         objs.append(obj)
         if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr) and not ptxas_info:
             continue
-        cmd = [nvcc, *ARCH, *COMMON, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
         if ptxas_info and src.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v")
         jobs.append(cmd)
@@ -67,15 +74,15 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp"
+    if jobs or not os.path.exists(lib):
+        tmp = lib + ".tmp"
         cmd = [nvcc, *ARCH, "-shared", "--cudart=static", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(verbose=True, ptxas_info="--ptxas" in sys.argv, debug="--debug" in sys.argv))

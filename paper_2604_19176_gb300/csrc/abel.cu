@@ -336,6 +336,9 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int jd = w % kTimeJ, sub = w / kTimeJ;   // sums and epilogues: detector, and chunks p = sub (mod kTimeSub)
     const int n_tc = in.n_tp >> 5, n_rc = in.n_rp >> 5;
+    // the staged rows hold the group's instance (the same for every CTA of the
+    // cluster, so all of them return here together and no cluster barrier waits)
+    if (!dbg_ok(dp, 32 * n_rc <= dp.time_rows_r && 32 * n_tc <= dp.time_rows_t, kSiteTimeRows)) return;
     const float* PT = dp.P + in.p_off + (size_t)in.n_tp * in.n_rp + lane;   // P^T: row m, pitch n_tp
     const float* PP = dp.P + in.p_off + lane;                               // P: row t, pitch n_rp
 
@@ -425,6 +428,7 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
                 const int c = time_chunk(p0 + u * kTimeSub, rank);
                 m[u] = 32 * c + lane;
                 cnt[u] = (c < n_rc && jok && m[u] < in.n_r) ? __ldg(cnt_row + m[u] / dp.m_lanes) : 0;
+                if (!dbg_ok(dp, cnt[u] <= in.n_slots, kSiteTimeRows)) cnt[u] = 0;
                 cmax = max(cmax, cnt[u]);
                 s[u] = 0.f;
             }

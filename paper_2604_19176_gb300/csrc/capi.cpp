@@ -109,6 +109,16 @@ cudaError_t circmean(Plan& p, const void* f, cudaStream_t st, bool msum = true)
     return e;
 }
 
+// The adjoint gather launch (list or cell form; f == nullptr: cell sums only,
+// for the fused steps); a bounds probe armed by pat_plan_set_bounds_probe
+// goes with this one launch only.
+cudaError_t gather(Plan& p, void* f, cudaStream_t st)
+{
+    const cudaError_t e = f ? launch_adjoint_gather(p.dp, f, st) : launch_adjoint_cells(p.dp, st);
+    p.dp.bounds_probe = 0;
+    return e;
+}
+
 bool valid_geometry(const pat_geometry_t& g, bool bf16)
 {
     if (g.n < 8 || g.n > 4096 || (g.n % (bf16 ? 8 : 4)) != 0) return false;
@@ -135,6 +145,7 @@ const char* pat_status_string(pat_status_t s)
     case PAT_ERR_UNSUPPORTED: return "PAT_ERR_UNSUPPORTED";
     case PAT_ERR_TIMEOUT: return "PAT_ERR_TIMEOUT";
     case PAT_ERR_BAD_PLAN: return "PAT_ERR_BAD_PLAN";
+    case PAT_ERR_BOUNDS: return "PAT_ERR_BOUNDS";
     }
     return "PAT_ERR_UNKNOWN";
 }
@@ -261,7 +272,7 @@ pat_status_t pat_adjoint(pat_plan_t h, const float* d_g, void* d_f, void* stream
     if (!ds.ok) return PAT_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(p->dp, d_g, st); });
-    if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return launch_adjoint_gather(p->dp, d_f, st); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return gather(*p, d_f, st); });
     return cuda_status(e);
 }
 
@@ -345,7 +356,7 @@ pat_status_t pat_tv_step(pat_plan_t h, const float* d_f_in, float* d_f_out, cons
         if (e == cudaSuccess)
             e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, p->d_resid, st); });
     }
-    if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return launch_adjoint_cells(dp, st); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return gather(*p, nullptr, st); });
     if (e == cudaSuccess)
         e = timed(*p, PAT_K_TV_UPDATE, st,
                   [&] { return launch_tv_update(dp, d_f_in, d_f_out, tau, lam, eps, nonneg, d_delta, st); });
@@ -409,7 +420,7 @@ pat_status_t pat_pdhg_step(pat_plan_t h, float* d_f, float* d_fbar, float* d_y, 
                       [&] { return launch_abel_fwd_dual(dp, d_y, d_g, sigma, inv1ps, st); });
         if (e == cudaSuccess) e = timed(*p, PAT_K_ABEL_ADJ, st, [&] { return launch_abel_adj(dp, d_y, st); });
     }
-    if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return launch_adjoint_cells(dp, st); });
+    if (e == cudaSuccess) e = timed(*p, PAT_K_ADJ_GATHER, st, [&] { return gather(*p, nullptr, st); });
     if (e == cudaSuccess)
         e = timed(*p, PAT_K_PDHG_PRIMAL, st,
                   [&] {
@@ -433,10 +444,33 @@ pat_status_t pat_plan_sync_status(pat_plan_t h, void* stream)
     if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
     if (word == 0) return PAT_OK;
     // a launch that gave up may have left counters armed: clear them with the word
+    // (a failed bounds check of a debug build is reported the same way)
     if (cudaMemsetAsync(p->dp.status, 0, sizeof(int32_t), st) != cudaSuccess) return PAT_ERR_CUDA;
     if (cudaMemsetAsync(p->d_counters, 0, p->counters_bytes, st) != cudaSuccess) return PAT_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return PAT_ERR_CUDA;
-    return PAT_ERR_TIMEOUT;
+    return (word & kBoundsFlag) ? PAT_ERR_BOUNDS : PAT_ERR_TIMEOUT;
+}
+
+pat_status_t pat_plan_set_bounds_probe(pat_plan_t h, int32_t enable)
+{
+    Plan* p = lookup(h);
+    if (!p) return PAT_ERR_BAD_PLAN;
+#ifdef PAT_DEBUG
+    p->dp.bounds_probe = enable ? 1 : 0;
+    return PAT_OK;
+#else
+    (void)enable;
+    return PAT_ERR_UNSUPPORTED;
+#endif
+}
+
+int32_t pat_debug_build(void)
+{
+#ifdef PAT_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 pat_status_t pat_plan_set_wait_probe(pat_plan_t h, int32_t clocks)

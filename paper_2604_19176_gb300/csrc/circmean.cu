@@ -83,6 +83,7 @@ __device__ __forceinline__ void stage_cells(float4* __restrict__ cells, const T*
 // bits into a byte offset of the staged cell.
 struct UnitFrame {
     uint32_t ulo, uhi, vlo, vhi, row_bytes, koff;
+    uint32_t lim;   // debug builds: largest valid byte offset of a staged cell
 };
 
 __device__ __forceinline__ UnitFrame unit_frame(const Segment& sg, const InstDev& in, float4 d)
@@ -105,7 +106,11 @@ __device__ __forceinline__ UnitFrame unit_frame(const Segment& sg, const InstDev
 // fma(m, hi, f0); -cell = kMagic - t (exact); a = fma(m, hi, -cell) +
 // fma(m, lo, f0).
 __device__ __forceinline__ float sample(const unsigned char* __restrict__ smem, const UnitFrame& u,
-                                        unsigned long long m2, float4 r, unsigned long long f0)
+                                        unsigned long long m2, float4 r, unsigned long long f0
+#ifdef PAT_DEBUG
+                                        , const DevPlan* dbg_plan
+#endif
+)
 {
     const unsigned long long hi = f2_pack(r.x, r.y), lo = f2_pack(r.z, r.w);
     const unsigned long long magic2 = f2_pack(kMagic, kMagic);
@@ -116,11 +121,21 @@ __device__ __forceinline__ float sample(const unsigned char* __restrict__ smem, 
     const float a = ab.x, b = ab.y;
     const uint32_t iu = min(max(__float_as_uint(tt.x), u.ulo), u.uhi);
     const uint32_t iv = min(max(__float_as_uint(tt.y), u.vlo), u.vhi);
-    const float4 c = *reinterpret_cast<const float4*>(smem + (iv * u.row_bytes + iu * 16u + u.koff));
+    const uint32_t off = iv * u.row_bytes + iu * 16u + u.koff;
+#ifdef PAT_DEBUG
+    if (!dbg_ok(*dbg_plan, off <= u.lim, kSiteCircCell)) return 0.f;
+#endif
+    const float4 c = *reinterpret_cast<const float4*>(smem + off);
     return fmaf(b, fmaf(a, c.w, c.z), fmaf(a, c.y, c.x));
 }
 
 } // namespace
+
+#ifdef PAT_DEBUG
+#define PAT_DBG_ARG , &dp
+#else
+#define PAT_DBG_ARG
+#endif
 
 template <int ML, typename T>
 __global__ void __launch_bounds__(kCircThreads, 2) k_circmean(DevPlan dp, const T* __restrict__ f)
@@ -146,6 +161,11 @@ __global__ void __launch_bounds__(kCircThreads, 2) k_circmean(DevPlan dp, const 
         const Segment sg = dp.segs[tidx];
         const InstDev in = dp.inst[sg.inst];
         __syncthreads(); // every warp is done with the previous tile
+
+        // the staged rays must fit behind the largest tile (uniform over the CTA)
+        if (!dbg_ok(dp, (int64_t)in.K * (int64_t)sizeof(float4) <= (int64_t)dp.fwd_smem_bytes - dp.fwd_rays_off,
+                    kSiteCircRays))
+            return;
 
         // ---- the instance's rays (TMA bulk copy; a plan table, so before the
         // dependency wait) and the tile's cells (from f, after it) -----------
@@ -178,22 +198,29 @@ __global__ void __launch_bounds__(kCircThreads, 2) k_circmean(DevPlan dp, const 
         for (int ui = ub; ui < ue; ++ui) {
             Unit un2{};
             if (ui + 1 < ue) un2 = dp.units[ui + 1];   // the next unit's record, in flight meanwhile
+            if (!dbg_ok(dp, un.j >= 0 && un.j < in.n_det && un.q0 >= 0 && un.nq >= 0 && un.q0 + un.nq <= in.K &&
+                                un.slot >= 0 && un.slot < in.n_slots && un.m0 >= 0,
+                        kSiteCircUnit)) {
+                un = un2;
+                continue;
+            }
             const int m = un.m0 + ml;
             const float mf = (float)m;
             const float4 d = __ldg(det + un.j);
-            const UnitFrame fr = unit_frame(sg, in, d);
+            UnitFrame fr = unit_frame(sg, in, d);
+            fr.lim = (uint32_t)((sg.y1 - sg.y0 + 3) * sg.pitch - 1) * 16u;
             const float4* tq = rays_s + un.q0 + ql;   // units never wrap past K
             const unsigned long long m2 = f2_pack(mf, mf), f0 = f2_pack(d.z, d.w);
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
             int i = ql;
             for (; i + 3 * QL < un.nq; i += 4 * QL, tq += 4 * QL) {
                 const float4 c0 = tq[0], c1 = tq[QL], c2 = tq[2 * QL], c3 = tq[3 * QL];
-                acc0 += sample(smem_raw, fr, m2, c0, f0);
-                acc1 += sample(smem_raw, fr, m2, c1, f0);
-                acc2 += sample(smem_raw, fr, m2, c2, f0);
-                acc3 += sample(smem_raw, fr, m2, c3, f0);
+                acc0 += sample(smem_raw, fr, m2, c0, f0 PAT_DBG_ARG);
+                acc1 += sample(smem_raw, fr, m2, c1, f0 PAT_DBG_ARG);
+                acc2 += sample(smem_raw, fr, m2, c2, f0 PAT_DBG_ARG);
+                acc3 += sample(smem_raw, fr, m2, c3, f0 PAT_DBG_ARG);
             }
-            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(smem_raw, fr, m2, *tq, f0);
+            for (; i < un.nq; i += QL, tq += QL) acc0 += sample(smem_raw, fr, m2, *tq, f0 PAT_DBG_ARG);
             float acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
             for (int o = ML; o < kWarp; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

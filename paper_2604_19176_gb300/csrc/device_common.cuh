@@ -83,6 +83,34 @@ __device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsig
 }
 
 // ---------------------------------------------------------------------------
+// Debug builds (-DPAT_DEBUG): device-side bounds checks.  dbg_ok(dp, ok, site)
+// returns ok; when ok is false it records kBoundsFlag | site in the plan's
+// status word (the first recorded error stays) and the caller skips the
+// access, so a bad index is reported by pat_plan_sync_status as
+// PAT_ERR_BOUNDS instead of trapping or faulting.  In release builds it is
+// the constant true and costs nothing.
+// ---------------------------------------------------------------------------
+enum BoundsSite : int32_t {
+    kSiteCircUnit = 1,     // circular-mean unit record (detector, angles, slot)
+    kSiteCircCell = 2,     // circular-mean staged-cell offset of a sample
+    kSiteCircRays = 3,     // circular-mean ray staging (shared-memory capacity)
+    kSiteListItem = 4,     // adjoint list item (instance, code vectors)
+    kSiteListEntry = 5,    // adjoint list entry (detector, ray, Mbar index)
+    kSiteTimeRows = 6,     // fused time stage rows and slots
+};
+__device__ __forceinline__ bool dbg_ok(const DevPlan& dp, bool ok, int32_t site)
+{
+#ifdef PAT_DEBUG
+    if (!ok && dp.status) atomicCAS(dp.status, 0, kBoundsFlag | site);
+    return ok;
+#else
+    (void)dp;
+    (void)site;
+    return true;
+#endif
+}
+
+// ---------------------------------------------------------------------------
 // Programmatic dependent launch.  Kernels of the operator chain are launched
 // with programmatic stream serialization, so the next kernel is launched as
 // soon as this one's CTAs exit (its launch overlaps the end of this one);

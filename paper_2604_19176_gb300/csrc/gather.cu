@@ -336,17 +336,39 @@ __global__ void __launch_bounds__(256, 4) k_adj_list(DevPlan dp)
             const int np = min(nx.nk, 4) * S;
             for (int u = 0; u < np; ++u) prefetch_l1(Ln + (size_t)u * kWarp);
         }
+        if (!dbg_ok(dp, it.inst >= 0 && it.inst < dp.n_inst && it.base >= 0 &&
+                            (LM == 1 || it.base + (int64_t)it.nk * kWarp <= dp.n_code_vecs),
+                    kSiteListItem))
+            continue;
         const InstDev in = dp.inst[it.inst];
         const int n = in.n, w = n + 1;
         const int cx = it.x0 + (lane & (kPatchW - 1)), cy = it.y0 + lane / kPatchW;
         if (cx > n - 1 || cy > n - 1) continue;
         const int cell = (cy + 1) * w + (cx + 1);
         const uint4* L = codes + it.base + lane;
+#ifdef PAT_DEBUG
+        // test hook: lane 0 of warp 0 gives its first entry a detector index past the instance's
+        // detectors (the tables it would address still lie inside the plan's allocations)
+        bool plant = dp.bounds_probe != 0 && warp == 0 && lane == 0 && ii == ib;
+        const uint32_t mb_size = (uint32_t)in.n_det * (uint32_t)in.m_pitch;
+#endif
         const float* mb = dp.mbar + in.mbar_off;
         Moments acc;
         if constexpr (LM == 1) {
             const int nv = (dp.cell_cnt[in.list_off + cell] + 3) >> 2;
             const int nk = (int)((int64_t)(it.group + 1) * nv / G) - (int)((int64_t)it.group * nv / G);
+            if (!dbg_ok(dp, it.base + (int64_t)nk * 3 * kWarp <= dp.n_code_vecs, kSiteListItem)) continue;
+#ifdef PAT_DEBUG
+            auto wload = [&](uint32_t i) {
+                if (plant) {
+                    i += mb_size;
+                    plant = false;
+                }
+                return dbg_ok(dp, i < mb_size, kSiteListEntry) ? __ldg(mb + i) : 0.f;
+            };
+#else
+            auto wload = [&](uint32_t i) { return __ldg(mb + i); };
+#endif
             // two vectors (8 entries) in flight per lane
             for (int kb = 0; kb < nk; kb += 2) {
                 uint4 ci[2], ca[2], cb[2];
@@ -364,10 +386,10 @@ __global__ void __launch_bounds__(256, 4) k_adj_list(DevPlan dp)
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     if (kb + u >= nk) break;
-                    acc.add(__ldg(mb + ci[u].x), __uint_as_float(ca[u].x), __uint_as_float(cb[u].x));
-                    acc.add(__ldg(mb + ci[u].y), __uint_as_float(ca[u].y), __uint_as_float(cb[u].y));
-                    acc.add(__ldg(mb + ci[u].z), __uint_as_float(ca[u].z), __uint_as_float(cb[u].z));
-                    acc.add(__ldg(mb + ci[u].w), __uint_as_float(ca[u].w), __uint_as_float(cb[u].w));
+                    acc.add(wload(ci[u].x), __uint_as_float(ca[u].x), __uint_as_float(cb[u].x));
+                    acc.add(wload(ci[u].y), __uint_as_float(ca[u].y), __uint_as_float(cb[u].y));
+                    acc.add(wload(ci[u].z), __uint_as_float(ca[u].z), __uint_as_float(cb[u].z));
+                    acc.add(wload(ci[u].w), __uint_as_float(ca[u].w), __uint_as_float(cb[u].w));
                 }
             }
         } else {
@@ -379,9 +401,25 @@ __global__ void __launch_bounds__(256, 4) k_adj_list(DevPlan dp)
             const int mbits = in.code_mbits, qshift = in.code_jbits + in.code_mbits;
             const uint32_t wmask = (1u << qshift) - 1u, mmask = (1u << mbits) - 1u;
             auto entry = [&](uint32_t c) {
+#ifndef PAT_DEBUG
                 const uint32_t widx = c & wmask;
+#endif
                 // (bit 31 is the pair flag in run-pair codes, the top bit of q in one-sample codes)
+#ifdef PAT_DEBUG
+                uint32_t widx = c & wmask;
+                const int q = (int)((LM == 2 ? c & 0x7fffffffu : c) >> qshift);
+                int j = (int)(widx >> mbits);
+                if (plant) {
+                    j += in.n_det;
+                    widx += mb_size;
+                    plant = false;
+                }
+                if (!dbg_ok(dp, j < in.n_det && q < 2 * in.K && widx + ((LM == 2 && (int32_t)c < 0) ? 1u : 0u) < mb_size,
+                            kSiteListEntry))
+                    return;
+#else
                 const int q = (int)((LM == 2 ? c & 0x7fffffffu : c) >> qshift), j = (int)(widx >> mbits);
+#endif
                 const float mf = __uint_as_float((c & mmask) | kMagicBits) - kMagic;   // m < 2^22
                 const float wv = __ldg(mb + widx);
                 const float4 d = __ldg(det + j);

@@ -151,6 +151,10 @@ struct ImgTile {
     int32_t inst, x0, y0, pad;
 };
 
+// Device status word values: small positive codes are bounded waits that
+// gave up; kBoundsFlag | site is a failed bounds check of a debug build.
+constexpr int32_t kBoundsFlag = 0x100;
+
 // Everything a kernel launch needs, by value (fits the 4 KB parameter space).
 struct DevPlan {
     const InstDev* inst;
@@ -194,6 +198,9 @@ struct DevPlan {
     int32_t fwd_rays_off;          // byte offset of the staged rays (after the largest tile)
     int32_t wait_probe;            // test hook: CTA 0 of the next circular-mean launch waits on a
                                    //   barrier nothing completes (bounded by wait_probe clocks)
+    int32_t bounds_probe;          // test hook (debug builds): the next list gather plants one
+                                   //   out-of-range detector index for its bounds check to report
+    int64_t n_code_vecs;           // adjoint lists: 16-byte vectors in the codes buffer
     int32_t abel_cluster_fwd;      // CTAs per cluster splitting each forward time contraction
     int32_t abel_cluster_adj;      // the same for the adjoint time contraction
     int32_t bf16;                  // image storage is BF16

@@ -1110,6 +1110,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         dp.list_items = reinterpret_cast<const ListItem*>(lb + o_items_l);
         dp.warp_items = reinterpret_cast<const int32_t*>(lb + o_witems_l);
         dp.codes = codes;
+        dp.n_code_vecs = (int64_t)(b_codes / 16);
         for (int i = 0; i < n_inst; ++i) {
             inst[i].list_off = tmpl_cnt_off[inst_tmpl[i]];
             inst[i].pbase_off = tmpl_pbase_off[inst_tmpl[i]];

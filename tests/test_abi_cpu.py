@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "pat.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:pat_status_t|const char\*)\s+(pat_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:pat_status_t|const char\*|int32_t)\s+(pat_\w+)\s*\(", text, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +43,23 @@ def test_library_exports_every_declared_symbol(lib):
 def test_status_strings(lib):
     assert lib.pat_status_string(0) == b"PAT_OK"
     assert lib.pat_status_string(6) == b"PAT_ERR_BAD_PLAN"
+    assert lib.pat_status_string(7) == b"PAT_ERR_BOUNDS"
     assert lib.pat_status_string(99) == b"PAT_ERR_UNKNOWN"
+
+
+def test_release_and_debug_builds(lib):
+    """The release library has no debug checks; the -DPAT_DEBUG build loads
+    (no GPU needed), exports the same symbols and says it is a debug build."""
+    from paper_2604_19176_gb300 import _lib, build
+
+    assert lib.pat_debug_build() == 0
+    assert lib.pat_plan_set_bounds_probe(None, 1) == 6
+    dbg = _lib.open_library(build.build(debug=True))
+    for name in declared_symbols():
+        assert hasattr(dbg, name), name
+    assert dbg.pat_debug_build() == 1
+    assert dbg.pat_plan_set_bounds_probe(None, 1) == 6
+    assert dbg.pat_forward(None, None, None, None) == 6
 
 
 def test_host_validation_without_gpu(lib):
