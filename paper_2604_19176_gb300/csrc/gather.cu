@@ -327,29 +327,22 @@ __global__ void __launch_bounds__(256, 4) k_adj_list(DevPlan dp)
     constexpr int S = LM == 1 ? 3 : 1;   // 16-byte slots per vector
     const uint4* codes = reinterpret_cast<const uint4*>(dp.codes);
     const int G = dp.adj_groups;
-    for (int ii = ib; ii < ie; ++ii) {
-        const ListItem it = dp.list_items[ii];
-        if (ii + 1 < ie) {
-            // the next item's first vectors, on their way while this item runs
-            const ListItem nx = dp.list_items[ii + 1];
-            const uint4* Ln = codes + nx.base + lane;
-            const int np = min(nx.nk, 4) * S;
-            for (int u = 0; u < np; ++u) prefetch_l1(Ln + (size_t)u * kWarp);
-        }
+    // one (patch, part) item; `first`: the warp's first item (the debug probe's entry)
+    auto run_item = [&](const ListItem& it, bool first) {
         if (!dbg_ok(dp, it.inst >= 0 && it.inst < dp.n_inst && it.base >= 0 &&
                             (LM == 1 || it.base + (int64_t)it.nk * kWarp <= dp.n_code_vecs),
                     kSiteListItem))
-            continue;
+            return;
         const InstDev in = dp.inst[it.inst];
         const int n = in.n, w = n + 1;
         const int cx = it.x0 + (lane & (kPatchW - 1)), cy = it.y0 + lane / kPatchW;
-        if (cx > n - 1 || cy > n - 1) continue;
+        if (cx > n - 1 || cy > n - 1) return;
         const int cell = (cy + 1) * w + (cx + 1);
         const uint4* L = codes + it.base + lane;
 #ifdef PAT_DEBUG
         // test hook: lane 0 of warp 0 gives its first entry a detector index past the instance's
         // detectors (the tables it would address still lie inside the plan's allocations)
-        bool plant = dp.bounds_probe != 0 && warp == 0 && lane == 0 && ii == ib;
+        bool plant = dp.bounds_probe != 0 && warp == 0 && lane == 0 && first;
         const uint32_t mb_size = (uint32_t)in.n_det * (uint32_t)in.m_pitch;
 #endif
         const float* mb = dp.mbar + in.mbar_off;
@@ -357,7 +350,7 @@ __global__ void __launch_bounds__(256, 4) k_adj_list(DevPlan dp)
         if constexpr (LM == 1) {
             const int nv = (dp.cell_cnt[in.list_off + cell] + 3) >> 2;
             const int nk = (int)((int64_t)(it.group + 1) * nv / G) - (int)((int64_t)it.group * nv / G);
-            if (!dbg_ok(dp, it.base + (int64_t)nk * 3 * kWarp <= dp.n_code_vecs, kSiteListItem)) continue;
+            if (!dbg_ok(dp, it.base + (int64_t)nk * 3 * kWarp <= dp.n_code_vecs, kSiteListItem)) return;
 #ifdef PAT_DEBUG
             auto wload = [&](uint32_t i) {
                 if (plant) {
@@ -462,7 +455,34 @@ __global__ void __launch_bounds__(256, 4) k_adj_list(DevPlan dp)
         }
         const float z10 = acc.sa - acc.sab, z01 = acc.sb - acc.sab;
         dp.zbuf[in.z_off + (size_t)it.group * w * w + cell] = make_float4(acc.s0 - acc.sa - z01, z10, z01, acc.sab);
+    };
+    // this warp's static items, then the shared tail of small items (largest
+    // first), whose next ticket is in flight while the current item runs
+    int ii = ib, tk = 0;
+    bool in_tail = false;
+    for (;;) {
+        int idx;
+        if (ii < ie) {
+            idx = ii++;
+            if (ii < ie) {
+                // the next item's first vectors, on their way while this item runs
+                const ListItem nx = dp.list_items[ii];
+                const uint4* Ln = codes + nx.base + lane;
+                const int np = min(nx.nk, 4) * S;
+                for (int u = 0; u < np; ++u) prefetch_l1(Ln + (size_t)u * kWarp);
+            }
+        } else {
+            if (dp.n_tail_items == 0) break;
+            if (!in_tail && lane == 0) tk = atomicAdd(dp.work_counters + kQueueStride, 1);
+            in_tail = true;
+            const int cur = __shfl_sync(0xffffffffu, tk, 0);
+            if (cur >= dp.n_tail_items) break;
+            if (lane == 0) tk = atomicAdd(dp.work_counters + kQueueStride, 1);
+            idx = dp.list_tail0 + cur;
+        }
+        run_item(dp.list_items[idx], idx == ib && !in_tail);
     }
+    if (dp.n_tail_items > 0) release_queue(dp.work_counters + kQueueStride, lane);
 }
 
 template <typename T>

@@ -201,6 +201,8 @@ struct DevPlan {
     int32_t bounds_probe;          // test hook (debug builds): the next list gather plants one
                                    //   out-of-range detector index for its bounds check to report
     int64_t n_code_vecs;           // adjoint lists: 16-byte vectors in the codes buffer
+    int32_t list_tail0;            // adjoint lists: list_items[list_tail0 ..] is the shared tail queue
+    int32_t n_tail_items;          //   of small items (largest first), after the per-warp items
     int32_t abel_cluster_fwd;      // CTAs per cluster splitting each forward time contraction
     int32_t abel_cluster_adj;      // the same for the adjoint time contraction
     int32_t bf16;                  // image storage is BF16

@@ -159,6 +159,7 @@ struct GeomTemplate {
 };
 
 constexpr double kUnitOverhead = 24.0; // per-unit fixed cost, in angle iterations
+constexpr double kListTailShare = 0.25; // list gather: share of the work in the shared tail queue
 
 // n pixels split into parts of at most w pixels, as equal as possible.
 std::vector<int> tile_edges(int n, int w)
@@ -1048,25 +1049,44 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         const int n_warps = lblocks * 8;
         std::vector<int32_t> warp_items(n_warps + 1, 0);
         std::vector<ListItem> sched(li.size());
+        int32_t n_tail = 0;
         {
             std::vector<int32_t> order(li.size());
             for (size_t k = 0; k < li.size(); ++k) order[k] = (int32_t)k;
             std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return li[a].nk > li[b].nk; });
+            // the smallest items, about kListTailShare of the work, form a shared
+            // queue that the warps drain after their own items: it absorbs the
+            // run-time spread the static cost model does not see (cache
+            // behaviour differs between regions of the image)
+            int64_t total = 0;
+            for (const ListItem& x : li) total += x.nk + 1;
+            size_t n_static = order.size();
+            for (int64_t tail_cost = 0; n_static > 0;) {
+                const int64_t c = li[order[n_static - 1]].nk + 1;
+                if ((double)(tail_cost + c) > kListTailShare * (double)total) break;
+                tail_cost += c;
+                --n_static;
+            }
+            n_tail = (int32_t)(order.size() - n_static);
             using Load = std::pair<int64_t, int32_t>;   // (cost, warp)
             std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
             for (int wv = 0; wv < n_warps; ++wv) heap.push({0, wv});
-            std::vector<int32_t> owner(li.size());
-            for (int32_t k : order) {
+            std::vector<int32_t> owner(li.size(), -1);
+            for (size_t r = 0; r < n_static; ++r) {
+                const int32_t k = order[r];
                 Load l = heap.top();
                 heap.pop();
                 owner[k] = l.second;
                 l.first += li[k].nk + 1;
                 heap.push(l);
             }
-            for (size_t k = 0; k < li.size(); ++k) ++warp_items[owner[k] + 1];
+            for (size_t k = 0; k < li.size(); ++k)
+                if (owner[k] >= 0) ++warp_items[owner[k] + 1];
             for (int wv = 0; wv < n_warps; ++wv) warp_items[wv + 1] += warp_items[wv];
             std::vector<int32_t> fill(warp_items.begin(), warp_items.end() - 1);
-            for (size_t k = 0; k < li.size(); ++k) sched[fill[owner[k]]++] = li[k];   // (li is in patch order)
+            for (size_t k = 0; k < li.size(); ++k)   // (li is in patch order)
+                if (owner[k] >= 0) sched[fill[owner[k]]++] = li[k];
+            for (size_t r = n_static; r < order.size(); ++r) sched[n_static + (r - n_static)] = li[order[r]];
         }
         const size_t b_pbase = sizeof(int64_t) * std::max<size_t>(pbase_all.size(), 1);
         const size_t b_cnt = sizeof(int32_t) * std::max<size_t>(cnt_all.size(), 1);
@@ -1146,6 +1166,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         }
         drop_seg();
         dp.n_list_items = (int)li.size();
+        dp.n_tail_items = n_tail;
+        dp.list_tail0 = (int)li.size() - n_tail;
         dp.adj_mode = list_mode;
         dp.adj_jblock = jblock;
         dp.cell_blocks = lblocks;
