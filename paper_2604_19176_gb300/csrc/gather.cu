@@ -318,7 +318,7 @@ __device__ __forceinline__ void prefetch_l1(const void* p)
 }
 
 template <int LM>
-__global__ void __launch_bounds__(256, 4) k_adj_list(DevPlan dp)
+__global__ void __launch_bounds__(256, 3) k_adj_list(DevPlan dp)
 {
     pdl_wait();   // Mbar comes from the previous kernel
     const int lane = threadIdx.x & 31;
