@@ -351,6 +351,17 @@ int32_t pat_debug_build(void);
 pat_status_t pat_plan_set_bounds_probe(pat_plan_t plan, int32_t enable);
 
 /*
+ * pat_debug_fail_alloc — test hook for the allocation-failure path of
+ * pat_plan_create (any build).  After pat_debug_fail_alloc(n), the n-th next
+ * device allocation made by plan creation or by the autotuner (n = 0: the
+ * next one) fails as if the device were out of memory, once; the call that
+ * made it then returns PAT_ERR_OOM (an autotuner candidate that fails is
+ * skipped instead) after freeing every allocation it had made.  n < 0
+ * disarms the hook.  Process-wide, for all devices; always returns PAT_OK.
+ */
+pat_status_t pat_debug_fail_alloc(int32_t n);
+
+/*
  * Per-kernel timing (tracing).  When enabled, every kernel the plan enqueues
  * is bracketed by a pair of CUDA events recorded on the launch stream.
  * pat_plan_kernel_times synchronises those events, adds their elapsed times

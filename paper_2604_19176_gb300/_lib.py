@@ -25,6 +25,7 @@ EXPORTED = (
     "pat_adjoint", "pat_tv_grad", "pat_residual", "pat_descent_step", "pat_plan_sync_status",
     "pat_plan_set_timing", "pat_plan_kernel_times", "pat_tv_grad_noalloc", "pat_tv_step", "pat_pdhg_step",
     "pat_plan_set_wait_probe", "pat_status_string", "pat_debug_build", "pat_plan_set_bounds_probe",
+    "pat_debug_fail_alloc",
 )
 KERNEL_KINDS = ("circmean", "abel_fwd", "abel_adj", "adjoint_gather", "tv", "residual", "descent", "tv_update",
                 "pdhg_dual", "pdhg_primal", "time_pair")
@@ -105,6 +106,7 @@ def open_library(path: str) -> ctypes.CDLL:
     lib.pat_plan_set_wait_probe.argtypes = [vp, i32]
     lib.pat_plan_set_bounds_probe.argtypes = [vp, i32]
     lib.pat_debug_build.argtypes = []
+    lib.pat_debug_fail_alloc.argtypes = [i32]
     lib.pat_plan_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i64p, i32]
     lib.pat_tv_grad_noalloc.argtypes = [vp, i32, i32, f32, vp, vp, vp]
     lib.pat_tv_step.argtypes = [vp, vp, vp, vp, f32, f32, f32, i32, vp, vp]

@@ -464,6 +464,12 @@ pat_status_t pat_plan_set_bounds_probe(pat_plan_t h, int32_t enable)
 #endif
 }
 
+pat_status_t pat_debug_fail_alloc(int32_t n)
+{
+    set_alloc_failure(n);
+    return PAT_OK;
+}
+
 int32_t pat_debug_build(void)
 {
 #ifdef PAT_DEBUG

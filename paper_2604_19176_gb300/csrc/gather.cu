@@ -407,9 +407,8 @@ __global__ void __launch_bounds__(256, 3) k_adj_list(DevPlan dp)
                     widx += mb_size;
                     plant = false;
                 }
-                if (!dbg_ok(dp, j < in.n_det && q < 2 * in.K && widx + ((LM == 2 && (int32_t)c < 0) ? 1u : 0u) < mb_size,
-                            kSiteListEntry))
-                    return;
+                const uint32_t wlast = widx + ((LM == 2 && (int32_t)c < 0) ? 1u : 0u);   // the pair's second weight
+                if (!dbg_ok(dp, j < in.n_det && q < 2 * in.K && wlast < mb_size, kSiteListEntry)) return;
 #else
                 const int q = (int)((LM == 2 ? c & 0x7fffffffu : c) >> qshift), j = (int)(widx >> mbits);
 #endif

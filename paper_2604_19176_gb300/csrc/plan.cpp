@@ -752,7 +752,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const size_t o_status = reserve(64);
     const size_t o_count = reserve(64);
     P.tables_bytes = off;
-    if (cudaMalloc(&P.d_tables, P.tables_bytes) != cudaSuccess) {
+    if (dev_malloc(&P.d_tables, P.tables_bytes) != cudaSuccess) {
         P.d_tables = nullptr;
         cudaGetLastError();
         return PAT_ERR_OOM;
@@ -789,7 +789,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     const int64_t o_res = ((o_ctr + n_ctr + 63) / 64) * 64;   // data residual of pat_tv_step
     const int64_t z_float_off = ((o_res + P.g_offsets[n_inst] + 63) / 64) * 64;
     P.work_floats = z_float_off + 4 * z_total;
-    if (cudaMalloc(&P.d_work, sizeof(float) * std::max<int64_t>(P.work_floats, 1)) != cudaSuccess) {
+    if (dev_malloc(reinterpret_cast<void**>(&P.d_work), sizeof(float) * std::max<int64_t>(P.work_floats, 1)) !=
+        cudaSuccess) {
         P.d_work = nullptr;
         cudaGetLastError();
         return PAT_ERR_OOM;
@@ -911,7 +912,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
             int64_t max_cells = 0;
             for (size_t t = 0; t < tmpls.size(); ++t)
                 max_cells = std::max<int64_t>(max_cells, (int64_t)(inst[rep[t]].n + 1) * (inst[rep[t]].n + 1));
-            if (cudaMalloc(&d_counts, sizeof(int32_t) * max_cells) != cudaSuccess) {
+            if (dev_malloc(reinterpret_cast<void**>(&d_counts), sizeof(int32_t) * max_cells) != cudaSuccess) {
                 cudaGetLastError();
                 return PAT_ERR_OOM;
             }
@@ -961,7 +962,8 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                 nblk[t] = (inst[rep[t]].n_det + jblock - 1) / jblock;
                 seg_off[t + 1] = seg_off[t] + patches_t * (nblk[t] + 1);
             }
-            if (cudaMalloc(&d_seg, sizeof(int32_t) * std::max<int64_t>(seg_off.back(), 1)) != cudaSuccess) {
+            if (dev_malloc(reinterpret_cast<void**>(&d_seg), sizeof(int32_t) * std::max<int64_t>(seg_off.back(), 1)) !=
+                cudaSuccess) {
                 cudaGetLastError();
                 return PAT_ERR_OOM;
             }
@@ -1104,7 +1106,7 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                 d_seg = nullptr;
             }
         };
-        if (cudaMalloc(&P.d_lists, list_bytes) != cudaSuccess) {
+        if (dev_malloc(&P.d_lists, list_bytes) != cudaSuccess) {
             P.d_lists = nullptr;
             cudaGetLastError();
             drop_seg();
@@ -1204,6 +1206,24 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
     I.device_bytes += list_bytes;
     I.bands_max = tiles_max;
     return PAT_OK;
+}
+
+namespace {
+std::atomic<int32_t> g_alloc_fail{-1};   // see set_alloc_failure
+} // namespace
+
+void set_alloc_failure(int32_t n) { g_alloc_fail.store(n < 0 ? -1 : n); }
+
+cudaError_t dev_malloc(void** p, size_t bytes)
+{
+    int32_t k = g_alloc_fail.load();
+    while (k >= 0 && !g_alloc_fail.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
 }
 
 void free_plan_memory(Plan& P)

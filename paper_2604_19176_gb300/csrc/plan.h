@@ -48,6 +48,13 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
                         cudaStream_t st);
 void free_plan_memory(Plan& P);
 
+// Every device allocation of plan creation (and of the autotuner) goes
+// through dev_malloc.  Test hook: after set_alloc_failure(n), the n-th next
+// such allocation (0 = the next one) fails as if the device were out of
+// memory, once; n < 0 disarms it.
+cudaError_t dev_malloc(void** p, size_t bytes);
+void set_alloc_failure(int32_t n);
+
 // Builds the plan with the fastest of a set of candidate tile shapes, timed on
 // the plan's geometries (tune = 1); results are cached per process.
 pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, const pat_options_t& opt,

@@ -131,11 +131,11 @@ pat_status_t autotune_plan(Plan** out, const pat_geometry_t* geoms, int n_inst, 
     }
     void* d_f = nullptr;
     float* d_g = nullptr;
-    if (cudaMalloc(&d_f, (size_t)f_elems * (bf16 ? 2 : 4)) != cudaSuccess) {
+    if (dev_malloc(reinterpret_cast<void**>(&d_f), (size_t)f_elems * (bf16 ? 2 : 4)) != cudaSuccess) {
         cudaGetLastError();
         return PAT_ERR_OOM;
     }
-    if (cudaMalloc(&d_g, (size_t)g_elems * 4) != cudaSuccess) {
+    if (dev_malloc(reinterpret_cast<void**>(&d_g), (size_t)g_elems * 4) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(d_f);
         return PAT_ERR_OOM;

@@ -44,6 +44,9 @@ def test_status_strings(lib):
     assert lib.pat_status_string(0) == b"PAT_OK"
     assert lib.pat_status_string(6) == b"PAT_ERR_BAD_PLAN"
     assert lib.pat_status_string(7) == b"PAT_ERR_BOUNDS"
+    # the allocation-failure hook is host state only: arming and disarming needs no GPU
+    assert lib.pat_debug_fail_alloc(3) == 0
+    assert lib.pat_debug_fail_alloc(-1) == 0
     assert lib.pat_status_string(99) == b"PAT_ERR_UNKNOWN"
 
 

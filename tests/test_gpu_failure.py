@@ -87,3 +87,42 @@ def test_wait_probe_argument_checks(cuda_dev):
     plan.set_wait_probe(0)                       # disarm: a no-op here
     plan.forward(torch.zeros(32, 32, device=cuda_dev))
     assert plan.sync_status() == PAT_OK
+
+
+def test_forced_allocation_failures_free_everything(cuda_dev):
+    """pat_debug_fail_alloc makes the k-th device allocation of the next plan
+    creation fail: every k up to the number of allocations returns
+    PAT_ERR_OOM with nothing left allocated, and past it the plan is built
+    and correct (host-side injection: nothing runs out on the GPU)."""
+    from paper_2604_19176_gb300 import _lib
+
+    lib = _lib.load()
+    g = Geometry(64, 16, 0.1, math.pi, 48, 2.0, 64)
+    f_np = inputs.random_image(64, seed=61).astype(np.float32)
+    ref_g = O.forward(og(g), f_np.astype(np.float64))
+    PatPlan(g, device=cuda_dev).close()   # first creation loads the kernels plan creation uses
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failed = 0
+    try:
+        for k in range(16):
+            assert lib.pat_debug_fail_alloc(k) == 0
+            try:
+                plan = PatPlan(g, device=cuda_dev)
+            except _lib.PatError as e:
+                assert e.status == 3, e.status             # PAT_ERR_OOM
+                torch.cuda.synchronize()
+                assert free0 - torch.cuda.mem_get_info()[0] < (1 << 20), k   # nothing leaked
+                failed += 1
+                continue
+            lib.pat_debug_fail_alloc(-1)                    # k was past the last allocation
+            out = plan.forward(torch.tensor(f_np, device=cuda_dev)).double().cpu().numpy()
+            assert plan.sync_status() == PAT_OK
+            assert rel(out, ref_g) <= 1e-5
+            plan.close()
+            break
+        else:
+            raise AssertionError("plan creation kept failing")
+    finally:
+        lib.pat_debug_fail_alloc(-1)
+    assert failed >= 3   # tables, workspace and the adjoint lists at least
