@@ -339,15 +339,27 @@ __global__ void __launch_bounds__(kTimeThreads, 2) k_time_pair(DevPlan dp, const
     // the staged rows hold the group's instance (the same for every CTA of the
     // cluster, so all of them return here together and no cluster barrier waits)
     if (!dbg_ok(dp, 32 * n_rc <= dp.time_rows_r && 32 * n_tc <= dp.time_rows_t, kSiteTimeRows)) return;
-    const float* PT = dp.P + in.p_off + (size_t)in.n_tp * in.n_rp + lane;   // P^T: row m, pitch n_tp
-    const float* PP = dp.P + in.p_off + lane;                               // P: row t, pitch n_rp
+    // P in 32 x 32 blocks (after P and P^T): forward [time chunk][radius
+    // block], then adjoint [radius chunk][time block]; float4 q of a block
+    // holds contraction rows 4q .. 4q + 3 of its 32 outputs in lane order
+    const size_t pplane = (size_t)in.n_tp * in.n_rp;
+    const float* PBF = dp.P + in.p_off + 2 * pplane;
+    const float* PBA = PBF + pplane;
 
-    // this lane's 32 values of P for block it (output 32 c + lane, rows 32 kc ..)
+    // this lane's 32 values of P for block it (output 32 c + lane, rows 32 kc ..): 8 16-byte loads,
+    // each a warp-wide 512-byte contiguous read
     auto load_block = [&](const TItem& it, float(&pv)[32]) {
-        const size_t pitch = it.phase == 0 ? in.n_tp : in.n_rp;
-        const float* src = (it.phase == 0 ? PT : PP) + 32 * it.c + (size_t)(32 * it.kc) * pitch;
+        const int nkc = it.phase == 0 ? n_rc : n_tc;   // contraction blocks per output chunk
+        const float4* src = reinterpret_cast<const float4*>(
+            (it.phase == 0 ? PBF : PBA) + ((size_t)it.c * nkc + it.kc) * 1024) + lane;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) pv[r] = __ldg(src + r * pitch);
+        for (int q = 0; q < 8; ++q) {
+            const float4 v = __ldg(src + q * 32);
+            pv[4 * q] = v.x;
+            pv[4 * q + 1] = v.y;
+            pv[4 * q + 2] = v.z;
+            pv[4 * q + 3] = v.w;
+        }
     };
     float acc[kTimeJ];
 #pragma unroll

@@ -53,7 +53,8 @@ struct InstDev {
     int64_t f_off, g_off;          // element offsets of the instance's image / data
     int64_t mpart_off;             // float offset of forward partial slots (n_slots x n_det x n_r)
     int64_t mbar_off;              // float offset of M and of Mbar (n_det rows of pitch m_pitch)
-    int64_t p_off;                 // float offset of P (n_t rows, pitch n_rp), then P^T (n_r rows, pitch n_tp)
+    int64_t p_off;                 // float offset of P (n_t rows, pitch n_rp), then P^T (n_r rows, pitch n_tp),
+                                   //   then both in 32 x 32 blocks (the fused time stage)
     int64_t slotcnt_off;           // byte offset of the slot counts (n_det x nmb int32)
     int64_t z_off;                 // float4 offset of the adjoint cell sums (groups x (n+1)^2)
     int64_t ray_off;               // entry offset of the instance's 2K rays and reciprocal rays

@@ -239,16 +239,28 @@ pat_status_t build_plan(Plan& P, const pat_geometry_t* geoms, int n_inst, const 
         const int nt = geoms[i].n_t;
         if (!p_off.count(nt)) {
             // P (ntp rows, pitch nrp) then P^T (nrp rows, pitch ntp); padding is
-            // zero, so the time kernels' 32-row chunks never leave the matrix
+            // zero, so the time kernels' 32-row chunks never leave the matrix.
+            // Then the same values in 32 x 32 blocks for the fused time stage,
+            // where lane l needs output 32 c + l over contraction rows r of the
+            // block: float4 q of a block holds rows 4q .. 4q + 3 of the 32
+            // outputs in lane order, so a warp reads each float4 as 512
+            // contiguous bytes.  Forward blocks (time chunk c, radius block kc),
+            // adjoint blocks (radius chunk c, time block kc).
             p_off[nt] = (int64_t)pmat.size();
             const int nr = nt + 2, nrp = (nr + 31) & ~31, ntp = (nt + 31) & ~31;
             std::vector<float> Pm = build_abel_matrix(nt);
-            const size_t base = pmat.size();
-            pmat.resize(base + 2 * (size_t)ntp * nrp, 0.0f);
+            const size_t base = pmat.size(), plane = (size_t)ntp * nrp;
+            pmat.resize(base + 4 * plane, 0.0f);
+            const size_t nbr = (size_t)nrp / 32, nbt = (size_t)ntp / 32;
             for (int kk = 0; kk < nt; ++kk)
                 for (int m = 0; m < nr; ++m) {
-                    pmat[base + (size_t)kk * nrp + m] = Pm[(size_t)kk * nr + m];
-                    pmat[base + (size_t)ntp * nrp + (size_t)m * ntp + kk] = Pm[(size_t)kk * nr + m];
+                    const float v = Pm[(size_t)kk * nr + m];
+                    pmat[base + (size_t)kk * nrp + m] = v;
+                    pmat[base + plane + (size_t)m * ntp + kk] = v;
+                    pmat[base + 2 * plane + ((kk / 32) * nbr + m / 32) * 1024 + ((m % 32) / 4 * 32 + kk % 32) * 4 +
+                         m % 4] = v;
+                    pmat[base + 3 * plane + ((m / 32) * nbt + kk / 32) * 1024 + ((kk % 32) / 4 * 32 + m % 32) * 4 +
+                         kk % 4] = v;
                 }
         }
     }
