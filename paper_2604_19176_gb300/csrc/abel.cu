@@ -237,7 +237,8 @@ cudaError_t launch_abel_adj(const DevPlan& dp, const float* g, cudaStream_t st)
 // owns one output for all kTimeJ detectors (kTimeJ accumulators; a row's
 // detector values are broadcast 16-byte shared-memory loads), and the block's 32
 // values of P for that output sit in registers, loaded one block ahead
-// (the loads of the first block are issued before the dependency wait: P
+// from the plan's blocked copy of P (8 warp-wide 512-byte loads per block;
+// the loads of the first block are issued before the dependency wait: P
 // does not depend on the data).  After a phase the warps' partial sums are
 // added in warp order (deterministic) and the epilogue runs.
 // ---------------------------------------------------------------------------

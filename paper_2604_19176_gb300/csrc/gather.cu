@@ -296,6 +296,11 @@ __global__ void k_fill_u32(uint32_t* __restrict__ p, int64_t n, uint32_t v)
 // detector and one ray load serve both samples).  The code lists are
 // aligned by detector blocks, so all lanes of an item have the same number
 // of vectors and, at any step, read the tables of a few detectors only.
+// Schedule: each warp first runs the items the plan assigned to it (LPT over
+// item lengths), then takes items from a shared queue of the smallest ones,
+// largest first (one atomic ticket per item, taken one item ahead; the last
+// warp to finish re-arms the counter).  Which warp runs an item does not
+// change any result: each (cell, part) is summed by one lane in list order.
 // ---------------------------------------------------------------------------
 namespace {
 struct Moments {
