@@ -176,6 +176,34 @@ def test_tv_value_and_gradient(cuda_dev):
         assert rel(grad[i].double().cpu().numpy(), rg) <= 1e-5
 
 
+def test_tv_grad_refuses_overlapping_buffers(cuda_dev):
+    """pat_tv_grad reads neighbouring pixels that other CTAs would already have
+    overwritten in place: a gradient overlapping the images, or a value buffer
+    inside either, is refused before anything is enqueued."""
+    import ctypes
+
+    from paper_2604_19176_gb300 import _lib
+
+    lib = _lib.load()
+    g = Geometry(64, 8, 0.0, math.pi, 16, 2.0, 16)
+    plan = PatPlan([g, g], device=cuda_dev)
+    f = torch.rand(2, 64, 64, device=cuda_dev)
+    grad = torch.empty_like(f)
+    val = torch.empty(2, device=cuda_dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(cuda_dev).cuda_stream)
+    p = lambda t, off=0: ctypes.c_void_p(t.data_ptr() + 4 * off)
+    e = ctypes.c_float(1e-2)
+    assert lib.pat_tv_grad(plan._h, p(f), e, p(f), p(val), stream) == 1           # in place
+    assert lib.pat_tv_grad(plan._h, p(f), e, p(f, 64), p(val), stream) == 1       # shifted by one row
+    assert lib.pat_tv_grad(plan._h, p(f), e, p(grad), p(f, 3), stream) == 1       # value inside the images
+    assert lib.pat_tv_grad(plan._h, p(f), e, p(grad), p(grad, 8), stream) == 1    # value inside the gradient
+    assert lib.pat_tv_grad(plan._h, p(f), e, p(grad), p(val), stream) == 0
+    torch.cuda.synchronize()
+    rv, rg = O.tv(f[1].double().cpu().numpy(), 1e-2)
+    assert abs(float(val[1]) - rv) <= 1e-5 * rv
+    assert rel(grad[1].double().cpu().numpy(), rg) <= 1e-5
+
+
 def test_residual_and_descent_step(cuda_dev):
     g = Geometry(40, 10, 0.0, math.pi, 20, 2.0, 16)
     plan = PatPlan(g, device=cuda_dev)
