@@ -309,3 +309,29 @@ def test_threads_do_not_change_forward(orc):
     orc.set_threads(1)
     assert np.array_equal(a, b)
     assert np.allclose(b1, b4, rtol=1e-14, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Symmetry of the whole operator under a quarter turn
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,n_det,K,start", [(24, 16, 32, 0.0), (17, 12, 20, 0.37), (32, 8, 64, 1.1)])
+def test_quarter_turn_equivariance(orc, n, n_det, K, start):
+    """Pixel (iy, ix) sits at (-1 + (ix+1/2)h, -1 + (iy+1/2)h) and detector j at
+    angle start + (j+1/2) 2 pi / n_det counter-clockwise from +x.  np.rot90
+    moves the content at (x, y) to (y, -x), a clockwise quarter turn about the
+    centre, under which the pixel grid and (with K divisible by 4) the angular
+    nodes map onto themselves.  So on a full circle with n_det divisible by 4,
+    A(rot90 f) is A f with the detector rows moved back by n_det/4, and A^T
+    commutes with the same pair of maps.  Catches swapped x/y, a mirrored
+    axis or a wrong detector orientation."""
+    g = geom(orc, n, n_det, 3 * n // 2, K, start=start)
+    f = inputs.random_image(n, seed=21).astype(np.float64)
+    a = orc.forward(g, f)
+    b = orc.forward(g, np.rot90(f, 1))
+    assert np.abs(b - np.roll(a, -n_det // 4, axis=0)).max() <= 1e-12 * np.abs(a).max()
+    assert np.abs(b - np.roll(a, n_det // 4, axis=0)).max() > 1e-3 * np.abs(a).max()   # not symmetric by chance
+    d = inputs.random_data(n_det, 3 * n // 2, seed=22).astype(np.float64)
+    fa = orc.adjoint(g, d)
+    fb = orc.adjoint(g, np.roll(d, -n_det // 4, axis=0))
+    assert np.abs(fb - np.rot90(fa, 1)).max() <= 1e-12 * np.abs(fa).max()
