@@ -79,3 +79,28 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.reference_arm(bench.parse(["--impl", "reference", "--gpus", "2"]))
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line with the GPU arm's
+    metric, unit and config keys, the steps it was asked for, and a
+    cpu_baseline and e2e object describing that same run."""
+    import json
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.reference_arm(bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "1"]))
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["higher_is_better"] is True
+    assert d["value"] > 0 and abs(d["value"] - 1000.0 / d["ms_per_step"]) <= 1e-6 * d["value"]
+    assert d["config"]["workload"] == "vessel256_half" and d["config"]["N"] == 256
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
