@@ -12,7 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "pat.h")).read()
+    with open(os.path.join(ROOT, "include", "pat.h")) as fh:
+        text = fh.read()
     return sorted(set(re.findall(r"^\s*(?:pat_status_t|const char\*|int32_t)\s+(pat_\w+)\s*\(", text, re.M)))
 
 

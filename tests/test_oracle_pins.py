@@ -157,7 +157,8 @@ def test_detector_convention_matches_paper_arcs(orc):
     """Cell-centred detectors: n detectors with the pitch of the full array
     cover n * pitch; 170 and 112 of 256-on-270-degrees give the printed
     179.30 and 118.125 degrees (Sec. 2.1, Sec. 2.4.2)."""
-    gold = json.load(open(os.path.join(GOLDEN, "detector_arcs.json")))
+    with open(os.path.join(GOLDEN, "detector_arcs.json")) as fh:
+        gold = json.load(fh)
     n_full, span = gold["n_full"], math.radians(gold["span_full_deg"])
     g = geom(orc, 64, n_full, 16, 16, span=span)
     xy = orc.detectors(g)

@@ -23,7 +23,7 @@ def test_unet_shapes_and_nonnegativity():
     x = torch.randn(1, 4, 32, 32)
     y = net(x)
     assert y.shape == (1, 1, 32, 32)
-    assert float(y.min()) >= 0.0
+    assert float(y.detach().min()) >= 0.0
     # encoder 8-16-32-64, decoder back to 8, head to 1
     assert net.enc[3][0].out_channels == 64 and net.dec[2][0].out_channels == 8
     m = UNet(in_ch=4, base=8, mouse=True)
