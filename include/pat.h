@@ -332,8 +332,7 @@ pat_status_t pat_plan_set_wait_probe(pat_plan_t plan, int32_t clocks);
  * error is kept) and the kernel carries on; it never traps.  The results of
  * that call are then undefined and pat_plan_sync_status reports
  * PAT_ERR_BOUNDS once, clearing the word.  Release builds compile the checks
- * out.  Such a check is the stand-in for a memory checker, which the GPUs
- * this library is developed on do not offer.
+ * out.  The checks serve where no device memory checker can be run.
  *
  * pat_debug_build — 1 when the library was compiled with -DPAT_DEBUG, else 0.
  *
